@@ -1,0 +1,356 @@
+"""Benchmark of validating UTF-16LE -> UTF-8 transcoding on GB300.
+
+Workload (one step = one call over the whole buffer): 256 MiB of UTF-16LE,
+20% U+0020-007E, 70% U+4E00-9FFF, 10% U+1F300-1FAFF as surrogate pairs
+(seeded synthetic text standing in for the paper's CJK/emoji files), fully
+validated and transcoded to UTF-8 by one kernel launch.  The input is larger
+than L2, so no flush is needed between steps.
+
+Prints one JSON line: input GB/s (device-timed, inputs resident in HBM), the
+same metric end to end through the host-buffer C-ABI call (copies included),
+the roofline of the kernel against the measured HBM copy bandwidth, SM clocks
+sampled during the timed region, and the CPU oracle's throughput on a sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank transcodes its own buffer (independent replicas; the
+path needs no exchange), and the reported value is all ranks' input bytes over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "validated UTF-8<->UTF-16 input GB/s, % of HBM roofline; serving p99 latency"
+WORKLOAD = "utf16le_to_utf8_validating_256MiB_cjk70_ascii20_emoji10"
+KERNEL = "utf16_to_utf8_kernel"
+KERNEL_SOURCES = ["paper_2109_10433_gb300/csrc/utf16_to_utf8.cu",
+                  "paper_2109_10433_gb300/csrc/common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "utf16_to_utf8_256MiB_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("source_hash") == kernel_source_hash():
+            return float(t["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of the GPU's SM clock and throttle reasons."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    c = [x.strip() for x in line.split(",")]
+                    if len(c) < 9:
+                        continue
+                    if self.uuid and c[0] != self.uuid:
+                        continue
+                    rows.append(c)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_baseline(data: np.ndarray, min_seconds: float):
+    """The oracle, as it stands, on the host cores: one thread."""
+    import oracle
+    oracle.build()
+    sample = data
+    runs, t0 = 0, time.perf_counter()
+    res = None
+    while True:
+        res = oracle.utf16_to_utf8(sample)[0]
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    assert res.error == 0
+    gbs = runs * sample.nbytes / el / 1e9
+    return gbs, runs, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    data = W.cjk_emoji_utf16_256mib()
+    # each step: the oracle over a bounded 32 MiB slice of the workload
+    k = (32 << 20) // 2
+    if 0xD800 <= int(data[k - 1]) <= 0xDBFF:   # do not split a surrogate pair
+        k -= 1
+    sample = data[:k]
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.utf16_to_utf8(sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.utf16_to_utf8(sample)[0]
+        times.append(time.perf_counter() - t0)
+        assert r.error == 0
+    total = sum(times)
+    value = args.steps * sample.nbytes / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "input_bytes": int(data.nbytes), "l2": "input larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 32 MiB of the 256 MiB workload per step, single thread"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2109_10433_gb300 as g
+    g.build()
+
+    data = W.cjk_emoji_utf16_256mib(seed=1 + rank)
+    n = data.size
+    inp = torch.from_numpy(data.view(np.int16)).to(dev)
+    out = torch.empty(3 * n, dtype=torch.uint8, device=dev)
+    ws = g.Workspace(n, device=dev)
+    res = torch.zeros(3, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = g.lib()
+    args_c = (g._ptr(inp), n, g._ptr(out), out.numel(), ws.ptr, ws.nbytes, g._ptr(res),
+              g._stream(stream))
+
+    def step():
+        st = L.gputf_utf16_to_utf8(*args_c)
+        if st != 0:
+            raise RuntimeError(f"gputf_utf16_to_utf8 status {st}")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    r = g.read_result(res)
+    assert r.error == 0 and r.position == n, r
+    out_bytes = r.written
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    region0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    region1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clock_info = clocks.stop() if clocks else None
+    r = g.read_result(res)
+    assert r.error == 0 and r.written == out_bytes, r
+
+    region_ms = region0.elapsed_time(region1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        t = torch.tensor([region_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        region_ms = float(t.item())
+    ms_per_step = region_ms / args.steps
+    value = world * args.steps * data.nbytes / (region_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer C-ABI call: pinned host input in,
+    # UTF-8 out to pinned host memory, result read back every step
+    h_in = torch.from_numpy(data.view(np.int16)).pin_memory()
+    h_out = torch.empty(3 * n, dtype=torch.uint8).pin_memory()
+    e2e_times = []
+    for i in range(args.e2e_warmup + args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = g.utf16_to_utf8_host(h_in, h_out, inp, out, ws, res)
+        el = time.perf_counter() - t0
+        assert rr.error == 0 and rr.written == out_bytes
+        if i >= args.e2e_warmup:
+            e2e_times.append(el)
+    e2e_total = max(sum(e2e_times), 1e-12)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_val = world * len(e2e_times) * data.nbytes / e2e_total / 1e9 if e2e_times else None
+
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peak()
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    algo_bytes = data.nbytes + out_bytes
+    achieved = algo_bytes / avg_launch_s / 1e9
+    traffic = ncu_traffic()
+    chars = int(np.count_nonzero((data & 0xFC00) != 0xDC00))
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        gbs, runs, el = cpu_oracle_baseline(data, args.cpu_seconds)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole 256 MiB buffer, {runs} run(s) in {el:.1f} s, single thread"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "input_bytes": int(data.nbytes),
+                   "output_bytes": int(out_bytes), "chars": chars,
+                   "l2": "input (256 MiB) larger than L2, no flush",
+                   "parallelism": f"replicas{world}"},
+        "gchar_s": world * args.steps * chars / (region_ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes": int(algo_bytes), "kernel": KERNEL,
+                     "avg_launch_us": avg_launch_s * 1e6, "peak_source": peak_kind},
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(data.nbytes),
+                "d2h_bytes_per_step": int(out_bytes + 24), "steps": len(e2e_times)},
+        "gpu_launches": args.steps,
+        "clocks": clock_info,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-warmup", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

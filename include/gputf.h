@@ -1,0 +1,170 @@
+/*
+ * gputf: validating UTF-8 <-> UTF-16LE transcoding on NVIDIA GB300 (sm_103a).
+ *
+ * The problem is the one stated by Lemire & Mula, "Transcoding Billions of
+ * Unicode Characters per Second with SIMD Instructions" (arXiv 2109.10433):
+ * transcode input in either UTF-8 or UTF-16 to the other encoding, with
+ * validation (Section 1), where validity is defined by the format rules of
+ * Section 3 (UTF-8 validation rules 1-6; UTF-16 surrogate pairs) and the
+ * transcoder reports how much input it consumed and how much output it
+ * wrote (Algorithm 3).
+ *
+ * Conventions shared by every call:
+ *   - Units.  Sizes and positions count code units of the encoding they refer
+ *     to: bytes for UTF-8, 16-bit units for UTF-16.  UTF-16 is little-endian;
+ *     no byte-order mark is detected or removed (U+FEFF is an ordinary
+ *     character), and U+0000 is an ordinary character.
+ *   - Memory.  `in`, `out`, the workspace and `res`/`len` are memory the
+ *     caller owns: device memory (for example from torch.empty on a CUDA
+ *     device), except that `res` and `len` may also be mapped pinned host
+ *     memory.  UTF-16 pointers must be 2-byte aligned, the workspace 16-byte
+ *     aligned, `res` and `len` 8-byte aligned; UTF-8 pointers need no
+ *     alignment.  No call allocates memory.
+ *   - Asynchrony.  Every call enqueues its work on `stream` and returns; the
+ *     result is written to `res` (or `len`) by the GPU.  Read it after the
+ *     stream has been synchronised.
+ *   - Workspace.  Calls that write output, validate or count use a workspace
+ *     of at least gputf_workspace_bytes(n) bytes, prepared once with
+ *     gputf_workspace_init().  The library keeps it ready for the next call
+ *     itself.  One workspace serves one call at a time: calls that share a
+ *     workspace must be ordered (for example, on one stream).
+ *   - Errors.  A gputf_status reports whether the call could be enqueued
+ *     (bad arguments, workspace too small, CUDA launch failure).  Whether the
+ *     data is valid is reported in the gputf_result.
+ */
+#ifndef GPUTF_H
+#define GPUTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *cudaStream_t;
+
+/* Data-level outcome (gputf_result.error).  Classes 1-6 follow the UTF-8
+ * validation rules of Section 3; UTF-16 input only ever reports
+ * GPUTF_SURROGATE.  When several rules fail on one character the class is
+ * taken in decoding order: the lead byte (TOO_LONG, HEADER_BITS), then
+ * missing continuation bytes (TOO_SHORT), then OVERLONG, TOO_LARGE,
+ * SURROGATE. */
+typedef enum gputf_error {
+    GPUTF_OK = 0,
+    GPUTF_HEADER_BITS = 1,       /* rule 1: a byte 0xF8..0xFF                         */
+    GPUTF_TOO_SHORT = 2,         /* rule 2: a lead without enough continuation bytes  */
+    GPUTF_TOO_LONG = 3,          /* rule 3: a continuation byte without a lead        */
+    GPUTF_OVERLONG = 4,          /* rule 4: a value that fits a shorter sequence      */
+    GPUTF_TOO_LARGE = 5,         /* rule 5: a value above U+10FFFF                    */
+    GPUTF_SURROGATE = 6,         /* rule 6 / Section 3: U+D800-DFFF, unpaired unit    */
+    GPUTF_OUTPUT_TOO_SMALL = 7,  /* the next character does not fit in `out`          */
+    GPUTF_TIMEOUT = 8,           /* a bounded wait between thread blocks ran out      */
+    GPUTF_INTERNAL = 9           /* internal inconsistency (never expected)           */
+} gputf_error;
+
+/* Call-level status (return value). */
+typedef enum gputf_status {
+    GPUTF_STATUS_OK = 0,
+    GPUTF_STATUS_INVALID_ARGUMENT = 1,   /* null pointer with n > 0, misaligned pointer */
+    GPUTF_STATUS_WORKSPACE_TOO_SMALL = 2,
+    GPUTF_STATUS_INPUT_TOO_LARGE = 3,    /* n above GPUTF_MAX_UNITS                      */
+    GPUTF_STATUS_CUDA_ERROR = 4,         /* a CUDA call failed (see gputf_last_cuda_error) */
+    GPUTF_STATUS_UNSUPPORTED_DEVICE = 5  /* the current device is not sm_103             */
+} gputf_status;
+
+/* Largest input, in code units, that one call accepts. */
+#define GPUTF_MAX_UNITS (((uint64_t)1) << 38)
+
+/* Result of a transcoding or validation call (written by the GPU).
+ *   error    : GPUTF_OK or the class of the first failure;
+ *   position : on success n; otherwise the offset, in input code units, of
+ *              the start of the first character that is invalid or does not
+ *              fit in the output (a stray continuation byte is its own start);
+ *   written  : output code units of the valid prefix [0, position), which
+ *              are exactly the transcoding of that prefix; output beyond them
+ *              is unspecified but never goes past the capacity.  Validation
+ *              calls write 0. */
+typedef struct gputf_result {
+    int32_t error;
+    int32_t reserved;
+    uint64_t position;
+    uint64_t written;
+} gputf_result;
+
+/* Workspace bytes needed for inputs of up to `max_units` code units. */
+size_t gputf_workspace_bytes(size_t max_units);
+
+/* Prepares a workspace (device memory, `ws_bytes` long) for use; enqueued on
+ * `stream`.  Needed once after allocation, and again after a call reported
+ * GPUTF_TIMEOUT. */
+gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Validating UTF-8 -> UTF-16LE (Sections 3-4).
+ *   in, n_bytes   : UTF-8 input (device), any alignment;
+ *   out, out_cap  : UTF-16LE output (device), capacity in 16-bit units; n_bytes
+ *                   units always suffice, gputf_utf16_length_from_utf8 gives the
+ *                   exact need of valid input;
+ *   res           : result (see gputf_result). */
+gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
+                                 void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+
+/* Validating UTF-16LE -> UTF-8 (Sections 3 and 5).
+ *   in, n_units   : UTF-16LE input (device, 2-byte aligned);
+ *   out, out_cap  : UTF-8 output (device), capacity in bytes; 3 * n_units
+ *                   always suffice, gputf_utf8_length_from_utf16 gives the
+ *                   exact need of valid input. */
+gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
+                                 void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+
+/* Validation only (Section 3, UTF-8 rules 1-6): res->error and res->position
+ * as for gputf_utf8_to_utf16, res->written = 0. */
+gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,
+                                 gputf_result *res, cudaStream_t stream);
+
+/* Validation only (Section 3, UTF-16 surrogate pairs). */
+gputf_status gputf_validate_utf16(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                  gputf_result *res, cudaStream_t stream);
+
+/* UTF-16 length of UTF-8 input, without validation (Table 2): one unit per
+ * byte that is not a continuation byte, plus one per byte >= 0xF0.  Equals
+ * the transcoded length when the input is valid. */
+gputf_status gputf_utf16_length_from_utf8(const uint8_t *in, size_t n_bytes, void *ws,
+                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream);
+
+/* UTF-8 length of UTF-16 input, without validation (Table 2): 1, 2 or 3 bytes
+ * per unit by value, 2 per surrogate unit.  Equals the transcoded length when
+ * the input is valid. */
+gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, void *ws,
+                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream);
+
+/* Host-buffer forms of the two transcoders, for callers whose text lives in
+ * host memory: copies `h_in` to the device buffer `d_in`, transcodes into
+ * `d_out`, copies the result struct to `h_res` and the `written` output units
+ * back to `h_out`.  Synchronous (returns after the copies are done).  The
+ * device buffers are the caller's (`d_in` holds the input, `d_out` out_cap
+ * units, `d_res` one gputf_result); pinned host memory makes the copies
+ * fastest. */
+gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
+                                      size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
+                                      size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                      cudaStream_t stream);
+gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
+                                      size_t out_cap, uint16_t *d_in, uint8_t *d_out, void *ws,
+                                      size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                      cudaStream_t stream);
+
+/* Names of codes, for messages. */
+const char *gputf_error_name(int32_t error);
+const char *gputf_status_name(gputf_status status);
+/* The last CUDA error code seen by a call on this thread (0 if none). */
+int gputf_last_cuda_error(void);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int gputf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPUTF_H */

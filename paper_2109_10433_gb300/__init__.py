@@ -1,0 +1,255 @@
+"""Python binding of libgputf: validating UTF-8 <-> UTF-16LE transcoding on
+NVIDIA GB300 (sm_103a).
+
+This module only marshals arguments: every step of the work runs in the CUDA
+kernels of libgputf.so, reached through its C ABI (include/gputf.h).  PyTorch
+provides device memory and streams.  There is no CPU fallback: if the library
+is not built, or the device is not an sm_103 part, calls raise.
+
+Two levels:
+  - `lib()` gives the raw ctypes functions, named as in the C header;
+  - the functions below (utf8_to_utf16, utf16_to_utf8, validate_utf8,
+    validate_utf16, utf16_length_from_utf8, utf8_length_from_utf16) take CUDA
+    tensors and a Workspace, enqueue the call on the current (or given)
+    stream and, unless sync=False, return the result read back from the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import NamedTuple
+
+from . import _build
+
+__all__ = [
+    "build", "lib", "Result", "Workspace", "GputfError",
+    "utf8_to_utf16", "utf16_to_utf8", "validate_utf8", "validate_utf16",
+    "utf16_length_from_utf8", "utf8_length_from_utf16",
+    "utf8_to_utf16_host", "utf16_to_utf8_host",
+    "ERROR_NAMES", "OK", "HEADER_BITS", "TOO_SHORT", "TOO_LONG", "OVERLONG", "TOO_LARGE",
+    "SURROGATE", "OUTPUT_TOO_SMALL", "TIMEOUT", "INTERNAL",
+]
+
+OK, HEADER_BITS, TOO_SHORT, TOO_LONG, OVERLONG, TOO_LARGE, SURROGATE = 0, 1, 2, 3, 4, 5, 6
+OUTPUT_TOO_SMALL, TIMEOUT, INTERNAL = 7, 8, 9
+ERROR_NAMES = ["OK", "HEADER_BITS", "TOO_SHORT", "TOO_LONG", "OVERLONG", "TOO_LARGE",
+               "SURROGATE", "OUTPUT_TOO_SMALL", "TIMEOUT", "INTERNAL"]
+STATUS_NAMES = ["OK", "INVALID_ARGUMENT", "WORKSPACE_TOO_SMALL", "INPUT_TOO_LARGE",
+                "CUDA_ERROR", "UNSUPPORTED_DEVICE"]
+
+LIB_PATH = _build.LIB
+
+# name -> (argtypes, restype); every entry point declared in include/gputf.h
+_P, _S, _I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+SIGNATURES = {
+    "gputf_workspace_bytes": ([_S], _S),
+    "gputf_workspace_init": ([_P, _S, _P], _I),
+    "gputf_utf8_to_utf16": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf16_to_utf8": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_validate_utf8": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_validate_utf16": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf16_length_from_utf8": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf8_length_from_utf16": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf8_to_utf16_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
+    "gputf_utf16_to_utf8_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
+    "gputf_error_name": ([ctypes.c_int32], ctypes.c_char_p),
+    "gputf_status_name": ([_I], ctypes.c_char_p),
+    "gputf_last_cuda_error": ([], _I),
+    "gputf_version": ([], _I),
+}
+
+
+class GputfError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile libgputf.so for sm_103a (nvcc) next to this file."""
+    return _build.build(force=force)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library, with ctypes signatures set.  Raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GputfError(f"{LIB_PATH} is not built: run paper_2109_10433_gb300.build() "
+                             "(nvcc for sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+class Result(NamedTuple):
+    error: int
+    position: int
+    written: int
+
+    @property
+    def ok(self) -> bool:
+        return self.error == OK
+
+    @property
+    def name(self) -> str:
+        return ERROR_NAMES[self.error] if 0 <= self.error < len(ERROR_NAMES) else "UNKNOWN"
+
+
+class _CResult(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("position", ctypes.c_uint64), ("written", ctypes.c_uint64)]
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        extra = f" (CUDA error {lib().gputf_last_cuda_error()})" if name == "CUDA_ERROR" else ""
+        raise GputfError(f"{what}: {name}{extra}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+
+
+class Workspace:
+    """Device scratch for the calls: a header and one status word per input
+    tile.  Owned by PyTorch's allocator; prepared once here."""
+
+    def __init__(self, max_units: int, device=None, stream=None):
+        torch = _torch()
+        self.max_units = int(max_units)
+        self.nbytes = int(lib().gputf_workspace_bytes(self.max_units))
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8,
+                               device=device if device is not None else "cuda")
+        _check(lib().gputf_workspace_init(_ptr(self.buf), self.nbytes, _stream(stream)),
+               "gputf_workspace_init")
+
+    @property
+    def ptr(self):
+        return _ptr(self.buf)
+
+    def reset(self, stream=None):
+        _check(lib().gputf_workspace_init(self.ptr, self.nbytes, _stream(stream)),
+               "gputf_workspace_init")
+
+
+def _res_tensor(res):
+    torch = _torch()
+    return res if res is not None else torch.empty(3, dtype=torch.int64, device="cuda")
+
+
+def read_result(res) -> Result:
+    """Reads a 24-byte result tensor (synchronises with the GPU)."""
+    v = res.cpu().tolist()
+    return Result(int(v[0]) & 0xFFFFFFFF, int(v[1]), int(v[2]))
+
+
+def _ws_for(ws, n):
+    if ws is None:
+        ws = Workspace(max(int(n), 1))
+    return ws
+
+
+def utf8_to_utf16(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True):
+    """UTF-8 bytes (CUDA uint8 tensor) -> UTF-16LE units.  Returns
+    (Result, out) when sync, else (res tensor, out); `out` defaults to n units
+    (torch.int16 storage)."""
+    torch = _torch()
+    n = inp.numel() * inp.element_size()
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int16, device=inp.device)
+    cap = out.numel() * out.element_size() // 2
+    ws, res = _ws_for(ws, n), _res_tensor(res)
+    _check(lib().gputf_utf8_to_utf16(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes,
+                                     _ptr(res), _stream(stream)), "gputf_utf8_to_utf16")
+    return (read_result(res) if sync else res), out
+
+
+def utf16_to_utf8(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True):
+    """UTF-16LE units (CUDA tensor of 2-byte elements) -> UTF-8 bytes.
+    `out` defaults to 3 bytes per unit (torch.uint8)."""
+    torch = _torch()
+    n = inp.numel() * inp.element_size() // 2
+    if out is None:
+        out = torch.empty(max(3 * n, 1), dtype=torch.uint8, device=inp.device)
+    cap = out.numel() * out.element_size()
+    ws, res = _ws_for(ws, n), _res_tensor(res)
+    _check(lib().gputf_utf16_to_utf8(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes,
+                                     _ptr(res), _stream(stream)), "gputf_utf16_to_utf8")
+    return (read_result(res) if sync else res), out
+
+
+def validate_utf8(inp, ws: Workspace | None = None, res=None, stream=None, sync=True):
+    n = inp.numel() * inp.element_size()
+    ws, res = _ws_for(ws, n), _res_tensor(res)
+    _check(lib().gputf_validate_utf8(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)),
+           "gputf_validate_utf8")
+    return read_result(res) if sync else res
+
+
+def validate_utf16(inp, ws: Workspace | None = None, res=None, stream=None, sync=True):
+    n = inp.numel() * inp.element_size() // 2
+    ws, res = _ws_for(ws, n), _res_tensor(res)
+    _check(lib().gputf_validate_utf16(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)),
+           "gputf_validate_utf16")
+    return read_result(res) if sync else res
+
+
+def _len_tensor(out):
+    torch = _torch()
+    return out if out is not None else torch.empty(1, dtype=torch.int64, device="cuda")
+
+
+def utf16_length_from_utf8(inp, ws: Workspace | None = None, out=None, stream=None, sync=True):
+    n = inp.numel() * inp.element_size()
+    ws, out = _ws_for(ws, n), _len_tensor(out)
+    _check(lib().gputf_utf16_length_from_utf8(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out),
+                                              _stream(stream)), "gputf_utf16_length_from_utf8")
+    return int(out.item()) if sync else out
+
+
+def utf8_length_from_utf16(inp, ws: Workspace | None = None, out=None, stream=None, sync=True):
+    n = inp.numel() * inp.element_size() // 2
+    ws, out = _ws_for(ws, n), _len_tensor(out)
+    _check(lib().gputf_utf8_length_from_utf16(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out),
+                                              _stream(stream)), "gputf_utf8_length_from_utf16")
+    return int(out.item()) if sync else out
+
+
+def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None) -> Result:
+    """Host-buffer form: h_in / h_out are CPU tensors (pinned for speed),
+    d_in / d_out / d_res device tensors of matching sizes."""
+    r = _CResult()
+    n = h_in.numel() * h_in.element_size()
+    cap = h_out.numel() * h_out.element_size() // 2
+    _check(lib().gputf_utf8_to_utf16_host(_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out),
+                                          ws.ptr, ws.nbytes, _ptr(d_res), ctypes.byref(r),
+                                          _stream(stream)), "gputf_utf8_to_utf16_host")
+    return Result(r.error, r.position, r.written)
+
+
+def utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None) -> Result:
+    r = _CResult()
+    n = h_in.numel() * h_in.element_size() // 2
+    cap = h_out.numel() * h_out.element_size()
+    _check(lib().gputf_utf16_to_utf8_host(_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out),
+                                          ws.ptr, ws.nbytes, _ptr(d_res), ctypes.byref(r),
+                                          _stream(stream)), "gputf_utf16_to_utf8_host")
+    return Result(r.error, r.position, r.written)

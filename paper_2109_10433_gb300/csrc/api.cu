@@ -1,0 +1,259 @@
+/*
+ * C-ABI entry points of libgputf (declared in include/gputf.h): argument
+ * checks, workspace sizing, device checks and kernel launches.  No entry
+ * point allocates memory.
+ */
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "gputf.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+struct DeviceInfo {
+    bool known = false;
+    bool supported = false;
+    int sms = 0;
+};
+
+constexpr int MAX_DEVICES = 64;
+DeviceInfo g_devices[MAX_DEVICES];
+std::mutex g_devices_mutex;
+
+gputf_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return GPUTF_STATUS_OK;
+    g_last_cuda_error = (int)e;
+    return GPUTF_STATUS_CUDA_ERROR;
+}
+
+/* The current device, checked to be an sm_103 part. */
+gputf_status current_device(int *sms)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return GPUTF_STATUS_UNSUPPORTED_DEVICE;
+    std::lock_guard<std::mutex> lock(g_devices_mutex);
+    DeviceInfo &d = g_devices[dev];
+    if (!d.known) {
+        int major = 0, minor = 0, count = 0;
+        if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_status(e);
+        d.supported = (major == 10 && minor == 3);
+        d.sms = count;
+        d.known = true;
+    }
+    if (!d.supported) return GPUTF_STATUS_UNSUPPORTED_DEVICE;
+    *sms = d.sms;
+    return GPUTF_STATUS_OK;
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+/* Checks shared by all calls; *status_words = tile-status capacity. */
+gputf_status check_common(const void *in, size_t n, void *ws, size_t ws_bytes, const void *res,
+                          uintptr_t in_align, uint64_t *status_words)
+{
+    if ((n > 0 && in == nullptr) || ws == nullptr || res == nullptr) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (!aligned(in, in_align) || !aligned(ws, 16) || !aligned(res, 8)) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if ((uint64_t)n > GPUTF_MAX_UNITS) return GPUTF_STATUS_INPUT_TOO_LARGE;
+    if (ws_bytes < gputf::HEADER_BYTES) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    *status_words = (ws_bytes - gputf::HEADER_BYTES) / 8;
+    return GPUTF_STATUS_OK;
+}
+
+__global__ void workspace_header_init(gputf::WsHeader *h)
+{
+    h->err_pos = gputf::NONE;
+    h->cap_pos = gputf::NONE;
+    h->epoch = 1;
+}
+
+}  // namespace
+
+namespace gputf {
+cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(ws, 0, bytes, s);
+    if (e != cudaSuccess) return e;
+    workspace_header_init<<<1, 1, 0, s>>>(static_cast<WsHeader *>(ws));
+    return cudaGetLastError();
+}
+}  // namespace gputf
+
+extern "C" {
+
+size_t gputf_workspace_bytes(size_t max_units)
+{
+    /* one status word per tile of at least 1024 units, plus the header */
+    uint64_t tiles = ((uint64_t)max_units + 16) / 1024 + 2;
+    return gputf::HEADER_BYTES + 8 * tiles;
+}
+
+gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (ws == nullptr || !aligned(ws, 16) || ws_bytes < gputf::HEADER_BYTES)
+        return GPUTF_STATUS_INVALID_ARGUMENT;
+    int sms;
+    gputf_status st = current_device(&sms);
+    if (st != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_workspace_init(ws, ws_bytes, stream));
+}
+
+gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
+                                 void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    if ((out_cap > 0 && out == nullptr) || !aligned(out, 2)) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (gputf::utf8_to_utf16_tiles(in, n_bytes) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
+                                                   reinterpret_cast<gputf::DevResult *>(res), stream));
+}
+
+gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
+                                 void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    if (out_cap > 0 && out == nullptr) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (gputf::utf16_to_utf8_tiles(in, n_units) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf16_to_utf8(in, n_units, out, out_cap, ws, words,
+                                                   reinterpret_cast<gputf::DevResult *>(res), stream));
+}
+
+gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,
+                                 gputf_result *res, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_validate_utf8(in, n_bytes, ws,
+                                                   reinterpret_cast<gputf::DevResult *>(res), sms, stream));
+}
+
+gputf_status gputf_validate_utf16(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                  gputf_result *res, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_validate_utf16(in, n_units, ws,
+                                                    reinterpret_cast<gputf::DevResult *>(res), sms, stream));
+}
+
+gputf_status gputf_utf16_length_from_utf8(const uint8_t *in, size_t n_bytes, void *ws,
+                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_bytes, ws, ws_bytes, len, 1, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf16_length_from_utf8(
+        in, n_bytes, ws, reinterpret_cast<unsigned long long *>(len), sms, stream));
+}
+
+gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, void *ws,
+                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_units, ws, ws_bytes, len, 2, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf8_length_from_utf16(
+        in, n_units, ws, reinterpret_cast<unsigned long long *>(len), sms, stream));
+}
+
+gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
+                                      size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
+                                      size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                      cudaStream_t stream)
+{
+    if ((n_bytes > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr ||
+        (out_cap > 0 && h_out == nullptr))
+        return GPUTF_STATUS_INVALID_ARGUMENT;
+    cudaError_t e;
+    if (n_bytes && (e = cudaMemcpyAsync(d_in, h_in, n_bytes, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_status(e);
+    gputf_status st = gputf_utf8_to_utf16(d_in, n_bytes, d_out, out_cap, ws, ws_bytes, d_res, stream);
+    if (st != GPUTF_STATUS_OK) return st;
+    if ((e = cudaMemcpyAsync(h_res, d_res, sizeof(gputf_result), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return cuda_status(e);
+    uint64_t w = h_res->written < out_cap ? h_res->written : out_cap;
+    if (w && (e = cudaMemcpyAsync(h_out, d_out, w * 2, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
+                                      size_t out_cap, uint16_t *d_in, uint8_t *d_out, void *ws,
+                                      size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                      cudaStream_t stream)
+{
+    if ((n_units > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr ||
+        (out_cap > 0 && h_out == nullptr))
+        return GPUTF_STATUS_INVALID_ARGUMENT;
+    cudaError_t e;
+    if (n_units &&
+        (e = cudaMemcpyAsync(d_in, h_in, n_units * 2, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_status(e);
+    gputf_status st = gputf_utf16_to_utf8(d_in, n_units, d_out, out_cap, ws, ws_bytes, d_res, stream);
+    if (st != GPUTF_STATUS_OK) return st;
+    if ((e = cudaMemcpyAsync(h_res, d_res, sizeof(gputf_result), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return cuda_status(e);
+    uint64_t w = h_res->written < out_cap ? h_res->written : out_cap;
+    if (w && (e = cudaMemcpyAsync(h_out, d_out, w, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+const char *gputf_error_name(int32_t error)
+{
+    static const char *names[] = {"OK",        "HEADER_BITS", "TOO_SHORT",        "TOO_LONG",
+                                  "OVERLONG",  "TOO_LARGE",   "SURROGATE",        "OUTPUT_TOO_SMALL",
+                                  "TIMEOUT",   "INTERNAL"};
+    return (error >= 0 && error <= 9) ? names[error] : "UNKNOWN";
+}
+
+const char *gputf_status_name(gputf_status status)
+{
+    switch (status) {
+    case GPUTF_STATUS_OK: return "OK";
+    case GPUTF_STATUS_INVALID_ARGUMENT: return "INVALID_ARGUMENT";
+    case GPUTF_STATUS_WORKSPACE_TOO_SMALL: return "WORKSPACE_TOO_SMALL";
+    case GPUTF_STATUS_INPUT_TOO_LARGE: return "INPUT_TOO_LARGE";
+    case GPUTF_STATUS_CUDA_ERROR: return "CUDA_ERROR";
+    case GPUTF_STATUS_UNSUPPORTED_DEVICE: return "UNSUPPORTED_DEVICE";
+    }
+    return "UNKNOWN";
+}
+
+int gputf_last_cuda_error(void) { return g_last_cuda_error; }
+
+int gputf_version(void) { return 100; }
+
+}  // extern "C"

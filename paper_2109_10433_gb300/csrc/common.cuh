@@ -1,0 +1,254 @@
+/*
+ * Device infrastructure shared by the kernels: the workspace layout, the
+ * tile-status words of the single-pass decoupled look-back scan, block-level
+ * scans and the "last CTA finishes the call" protocol.
+ *
+ * Output offsets.  Every kernel that writes output turns per-character output
+ * lengths into output offsets in one pass over the input.  The paper's
+ * conclusion suggests decoding pieces of a string independently once the
+ * character offsets are known; here each tile of the input computes its own
+ * output length, publishes it, and learns the total of all earlier tiles by
+ * looking back over their published words (Merrill & Garland, "Single-pass
+ * Parallel Prefix Scan with Decoupled Look-back", 2016).
+ *
+ * Tiles are taken in order from a ticket counter, so a tile only ever waits
+ * for tiles that started before it: no deadlock whatever the residency.  Every
+ * wait is bounded; a wait that runs out records a timeout in the workspace
+ * header and the call reports GPUTF_TIMEOUT.
+ *
+ * The workspace cleans itself: the CTA that finishes last resets the ticket
+ * and done counters and the error words, and moves the epoch on.  Status
+ * words carry the epoch of the call that wrote them, so words left by an
+ * earlier call are never read as current and need no clearing between calls.
+ */
+#ifndef GPUTF_COMMON_CUH
+#define GPUTF_COMMON_CUH
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "utf8_scheme.h"
+
+namespace gputf {
+
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+constexpr uint64_t NONE = ~0ull;
+
+/* Workspace header, at the start of the caller's workspace. */
+struct WsHeader {
+    unsigned long long ticket;    /* next tile ticket                          */
+    unsigned long long done;      /* CTAs that finished                        */
+    unsigned long long err_pos;   /* first flagged input position, NONE if none */
+    unsigned long long cap_pos;   /* first character whose output does not fit */
+    unsigned long long accum;     /* sum of a length pass                      */
+    unsigned int epoch;           /* current call epoch, 1 .. EPOCH_LIMIT-1    */
+    unsigned int flags;           /* FLAG_TIMEOUT                              */
+    unsigned long long reserved[26];
+};
+static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
+
+constexpr unsigned FLAG_TIMEOUT = 1u;
+constexpr size_t HEADER_BYTES = 256;
+
+/* Tile status word: epoch (22 bits) | flag (2 bits) | value (40 bits). */
+constexpr unsigned EPOCH_BITS = 22;
+constexpr unsigned EPOCH_LIMIT = 1u << EPOCH_BITS;
+constexpr uint64_t VALUE_MASK = (1ull << 40) - 1;
+constexpr uint64_t ST_AGGREGATE = 1;   /* value = this tile's own total            */
+constexpr uint64_t ST_PREFIX = 2;      /* value = total of this tile and all before */
+
+__device__ __forceinline__ uint64_t make_status(unsigned epoch, uint64_t flag, uint64_t value)
+{
+    return ((uint64_t)epoch << 42) | (flag << 40) | (value & VALUE_MASK);
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire(const unsigned long long *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+/* Upper bound on polls of one status word (with back-off, about a second). */
+constexpr int SPIN_LIMIT = 1 << 21;
+
+/*
+ * Exclusive prefix of tile `tile` by decoupled look-back.  Called by all 32
+ * lanes of one warp after the tile's aggregate has been published.  Each lane
+ * reads one predecessor; the window moves back 32 tiles at a time until it
+ * meets a tile that published its inclusive prefix.
+ */
+__device__ __forceinline__ uint64_t look_back(unsigned long long *status, long long tile,
+                                              unsigned epoch, unsigned *flags)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t exclusive = 0;
+    long long end = tile - 1;     /* newest predecessor in the window */
+    while (end >= 0) {
+        long long idx = end - lane;
+        uint64_t flag = ST_PREFIX, value = 0;
+        if (idx >= 0) {
+            int spins = 0;
+            unsigned ns = 32;
+            while (true) {
+                uint64_t w = ld_acquire(status + idx);
+                if ((unsigned)(w >> 42) == epoch && ((w >> 40) & 3) != 0) {
+                    flag = (w >> 40) & 3;
+                    value = w & VALUE_MASK;
+                    break;
+                }
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    flag = ST_PREFIX;
+                    value = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 512) ns <<= 1;
+            }
+        }
+        unsigned pmask = __ballot_sync(FULL_MASK, flag == ST_PREFIX);
+        /* lanes up to and including the nearest inclusive prefix count */
+        int stop = pmask ? __ffs(pmask) - 1 : 31;
+        uint64_t v = lane <= stop ? value : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        exclusive += v;
+        if (pmask) break;
+        end -= 32;
+    }
+    return exclusive;
+}
+
+/* Inclusive warp scan of 32-bit values. */
+__device__ __forceinline__ uint32_t warp_inclusive(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL_MASK, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+/*
+ * Block-wide exclusive scan of one 32-bit value per thread.  `warp_sums`
+ * holds at least THREADS/32 words of shared memory.  Returns the thread's
+ * exclusive prefix; *total gets the block total.  Contains __syncthreads().
+ */
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *warp_sums, uint32_t *total)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_inclusive(v);
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < WARPS ? warp_sums[lane] : 0;
+        uint32_t si = warp_inclusive(s);
+        if (lane < WARPS) warp_sums[lane] = si - s;
+        if (lane == 31) warp_sums[WARPS] = si;
+    }
+    __syncthreads();
+    *total = warp_sums[WARPS];
+    return warp_sums[warp] + inc - v;
+}
+
+/* Block-wide minimum of 64-bit values into *out (shared); contains syncs. */
+template <int THREADS>
+__device__ __forceinline__ uint64_t block_min(uint64_t v, unsigned long long *scratch)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t t = __shfl_xor_sync(FULL_MASK, v, o);
+        v = t < v ? t : v;
+    }
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    uint64_t m = scratch[0];
+#pragma unroll
+    for (int w = 1; w < WARPS; w++) m = scratch[w] < m ? scratch[w] : m;
+    __syncthreads();
+    return m;
+}
+
+/* Marks this CTA done; returns true (to every thread) in the CTA that
+ * finished last.  Everything the CTA wrote before is visible to that CTA. */
+__device__ __forceinline__ bool finish_cta(WsHeader *h, unsigned *smem_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned long long prev = atomicAdd(&h->done, 1ull);
+        *smem_flag = (prev == (unsigned long long)gridDim.x - 1) ? 1u : 0u;
+        if (*smem_flag) __threadfence();
+    }
+    __syncthreads();
+    return *smem_flag != 0;
+}
+
+/* Reset the header for the next call (last CTA only) and advance the epoch.
+ * When the epoch would wrap, every status word is cleared first. */
+__device__ __forceinline__ void reset_workspace(WsHeader *h, unsigned long long *status,
+                                                uint64_t status_words)
+{
+    unsigned next = h->epoch + 1;
+    if (next >= EPOCH_LIMIT) {
+        for (uint64_t i = threadIdx.x; i < status_words; i += blockDim.x) status[i] = 0;
+        next = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        h->ticket = 0;
+        h->done = 0;
+        h->err_pos = NONE;
+        h->cap_pos = NONE;
+        h->accum = 0;
+        h->flags = 0;
+        h->epoch = next;
+        __threadfence();
+    }
+}
+
+/* Non-caching 16-byte global load (streamed input). */
+__device__ __forceinline__ uint4 ld_stream16(const void *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+/* Streaming 16-byte global store. */
+__device__ __forceinline__ void st_stream16(void *p, uint4 v)
+{
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int k)
+{
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+}  // namespace gputf
+
+#endif

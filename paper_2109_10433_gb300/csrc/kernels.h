@@ -1,0 +1,37 @@
+/* Internal interface between the C-ABI layer (api.cu) and the kernels. */
+#ifndef GPUTF_KERNELS_H
+#define GPUTF_KERNELS_H
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gputf {
+
+/* Same layout as gputf_result in the public header. */
+struct DevResult {
+    int32_t error;
+    int32_t reserved;
+    uint64_t position;
+    uint64_t written;
+};
+
+uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n);
+uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n);
+
+cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res, cudaStream_t s);
+cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res, cudaStream_t s);
+cudaError_t launch_validate_utf8(const uint8_t *in, uint64_t n, void *ws, DevResult *res, int sms,
+                                 cudaStream_t s);
+cudaError_t launch_validate_utf16(const uint16_t *in, uint64_t n, void *ws, DevResult *res, int sms,
+                                  cudaStream_t s);
+cudaError_t launch_utf16_length_from_utf8(const uint8_t *in, uint64_t n, void *ws,
+                                          unsigned long long *len, int sms, cudaStream_t s);
+cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *ws,
+                                          unsigned long long *len, int sms, cudaStream_t s);
+cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s);
+
+}  // namespace gputf
+
+#endif

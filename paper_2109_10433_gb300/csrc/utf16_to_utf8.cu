@@ -1,0 +1,483 @@
+/*
+ * Validating UTF-16LE -> UTF-8, and the UTF-16 validate-only and length-only
+ * passes.
+ *
+ * One CTA transcodes one tile of TILE input units (tiles in ticket order):
+ *   1. load: each thread reads UPT consecutive units with aligned 16-byte
+ *      loads (the tile grid is aligned to 16 bytes below the input pointer),
+ *      plus the unit before and the unit after its chunk from the
+ *      neighbouring lanes or, at warp edges, from memory;
+ *   2. validate (Section 3): a high surrogate D800-DBFF must be followed by a
+ *      low surrogate DC00-DFFF and a low surrogate must follow a high one;
+ *      threads whose units hold no surrogate skip the check (it cannot fail
+ *      there), as the paper only validates where surrogates appear;
+ *   3. per-unit output length (Section 5's four cases): 1 byte below 0x80,
+ *      2 below 0x800, 3 for the rest of the BMP, and 2 for each surrogate
+ *      unit, so that a pair yields its 4 bytes; summed per thread, scanned
+ *      over the block and over earlier tiles by decoupled look-back;
+ *   4. encode each unit (lead prefixes 110 / 1110 / 11110 and continuation
+ *      prefix 10 over 5/4/3 + 6-bit groups): the high unit of a pair emits
+ *      the first two bytes of the character (F0 | c >> 18, 80 | c >> 12 & 3F,
+ *      with c >> 10 = (high & 0x3FF) + 0x40) and the low unit the last two,
+ *      so every unit writes independently.  Each thread packs its bytes into
+ *      32-bit words of a shared-memory staging buffer aligned like the
+ *      output, then the tile's range is written with aligned 16-byte stores;
+ *   5. the first invalid unit (exact: no fix-up is needed in UTF-16) goes to
+ *      an atomicMin; the CTA that finishes last writes the result.
+ */
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gputf {
+
+__device__ __forceinline__ uint32_t unit_at(const uint16_t *base, long long ex, uint64_t head,
+                                            uint64_t endx)
+{
+    return (ex >= (long long)head && ex < (long long)endx) ? base[ex] : 0u;
+}
+
+/* Two units at extended index ex (even), zero outside. */
+__device__ __forceinline__ uint32_t pair_at(const uint16_t *base, long long ex, uint64_t head,
+                                            uint64_t endx)
+{
+    if (ex >= (long long)head && ex + 2 <= (long long)endx)
+        return *reinterpret_cast<const uint32_t *>(base + ex);
+    return unit_at(base, ex, head, endx) | (unit_at(base, ex + 1, head, endx) << 16);
+}
+
+/* Loads one thread's chunk of 2*WORDS units; true when wholly inside. */
+template <int WORDS>
+__device__ __forceinline__ bool load_chunk16(const uint16_t *base, uint64_t e0, uint64_t head,
+                                             uint64_t endx, uint32_t (&w)[WORDS])
+{
+    const bool interior = e0 >= head && e0 + 2 * WORDS <= endx;
+    if (interior) {
+#pragma unroll
+        for (int v = 0; v < WORDS / 4; v++) {
+            uint4 q = ld_stream16(base + e0 + 8 * v);
+            w[4 * v + 0] = q.x;
+            w[4 * v + 1] = q.y;
+            w[4 * v + 2] = q.z;
+            w[4 * v + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = pair_at(base, (long long)(e0 + 2 * k), head, endx);
+    }
+    return interior;
+}
+
+__device__ __forceinline__ bool is_high(uint32_t u) { return (u & 0xFC00) == 0xD800; }
+__device__ __forceinline__ bool is_low(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
+
+/* Any unit of the two in x in D800-DFFF? */
+__device__ __forceinline__ bool has_surrogate(uint32_t x)
+{
+    const uint32_t y = (x & 0xF800F800u) ^ 0xD800D800u;   /* a zero half = surrogate */
+    return ((y - 0x00010001u) & ~y & 0x80008000u) != 0;
+}
+
+/* UTF-8 bytes of unit u (byte 0 first, little-endian in the word) and their
+ * count; `prev` is the unit before u, used when u is a low surrogate. */
+__device__ __forceinline__ uint32_t encode_unit(uint32_t u, uint32_t prev, int *len)
+{
+    const uint32_t two = (u >> 6) | ((u & 0x3F) << 8) | 0x80C0u;
+    const uint32_t three = (u >> 12) | (((u >> 6) & 0x3F) << 8) | ((u & 0x3F) << 16) | 0x8080E0u;
+    const uint32_t ch = (u & 0x3FF) + 0x40;                  /* code point >> 10, from a high unit */
+    const uint32_t high = (ch >> 8) | (((ch >> 2) & 0x3F) << 8) | 0x80F0u;
+    const uint32_t cp = (prev & 0x3FF) + 0x40;               /* code point >> 10, from the unit before */
+    const uint32_t low = ((cp & 3) << 4) | ((u >> 6) & 0xF) | ((u & 0x3F) << 8) | 0x8080u;
+    const bool sur = (u & 0xF800) == 0xD800;
+    *len = u < 0x80 ? 1 : ((u < 0x800 || sur) ? 2 : 3);
+    return u < 0x80 ? u : (u < 0x800 ? two : (sur ? ((u & 0x400) ? low : high) : three));
+}
+
+/* Append `len` bytes held in `v` to a thread's run of staged bytes.  Full
+ * words are stored; the first word (when the run starts inside a word) and
+ * the last partial word are shared with the neighbouring threads' runs and
+ * are OR-ed into the zeroed staging buffer. */
+struct Packer {
+    unsigned long long acc;
+    uint32_t nbits;
+    uint32_t widx;
+    bool first_shared;
+    __device__ __forceinline__ void start(uint32_t byte_pos)
+    {
+        acc = 0;
+        nbits = 8 * (byte_pos & 3);
+        widx = byte_pos >> 2;
+        first_shared = (byte_pos & 3) != 0;
+    }
+    __device__ __forceinline__ void put(uint32_t *stage, uint32_t v, int len)
+    {
+        acc |= (unsigned long long)v << nbits;
+        nbits += 8 * len;
+        if (nbits >= 32) {
+            if (first_shared)
+                atomicOr(stage + widx, (uint32_t)acc);
+            else
+                stage[widx] = (uint32_t)acc;
+            first_shared = false;
+            widx++;
+            acc >>= 32;
+            nbits -= 32;
+        }
+    }
+    __device__ __forceinline__ void finish(uint32_t *stage)
+    {
+        if (nbits) atomicOr(stage + widx, (uint32_t)acc);
+    }
+};
+
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
+                     uint64_t cap, WsHeader *hdr, unsigned long long *status,
+                     uint64_t status_words, DevResult *res)
+{
+    constexpr int UPT = 2 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    constexpr int WARPS = THREADS / 32;
+    constexpr uint32_t STAGE_WORDS = (uint32_t)((3 * TILE + 16) / 4);
+    __shared__ uint32_t s_warp[WARPS + 1];
+    __shared__ unsigned long long s_min[WARPS];
+    __shared__ unsigned long long s_tile_excl;
+    __shared__ unsigned s_tile, s_flag;
+    extern __shared__ uint4 s_stage4[];
+    uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage4);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = (unsigned)atomicAdd(&hdr->ticket, 1ull);
+    for (uint32_t i = tid; i < STAGE_WORDS / 4; i += THREADS) s_stage4[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
+
+    const uint64_t head = ((uintptr_t)in & 15) / 2;
+    const uint16_t *base = in - head;
+    const uint64_t endx = head + n;
+    const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
+
+    /* 1. load */
+    uint32_t w[WORDS];
+    const bool interior = load_chunk16<WORDS>(base, e0, head, endx, w);
+    uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
+    uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
+    if (lane == 0) pu = unit_at(base, (long long)e0 - 1, head, endx);
+    if (lane == 31) nu = unit_at(base, (long long)(e0 + UPT), head, endx);
+
+    /* which units are input units (edge chunks only) */
+    uint32_t inr = (1u << UPT) - 1;
+    if (!interior) {
+        inr = 0;
+#pragma unroll
+        for (int k = 0; k < UPT; k++) {
+            const long long ex = (long long)(e0 + k);
+            inr |= (ex >= (long long)head && ex < (long long)endx) ? (1u << k) : 0u;
+        }
+    }
+
+    /* 3. lengths; 2. any surrogate / all ASCII */
+    uint32_t total = 0;
+    bool sur = false;
+    uint32_t any = 0;
+#pragma unroll
+    for (int k = 0; k < WORDS; k++) {
+        const uint32_t x = w[k];
+        any |= x;
+        sur |= has_surrogate(x);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t u = (x >> (16 * h)) & 0xFFFF;
+            const uint32_t l = u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
+            total += (inr >> (2 * k + h)) & 1 ? l : 0;
+        }
+    }
+    const bool ascii = (any & 0xFF80FF80u) == 0;
+
+    /* 2. validation where surrogates appear */
+    uint64_t first_err = NONE;
+    if (sur) {
+        uint32_t prev = pu;
+#pragma unroll
+        for (int k = 0; k < UPT; k++) {
+            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
+            const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
+            const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
+            if (bad && ((inr >> k) & 1) && first_err == NONE) first_err = e0 + k - head;
+            prev = u;
+        }
+    }
+
+    /* block scan and look-back */
+    uint32_t tile_total;
+    const uint32_t excl_local = block_exclusive<THREADS>(total, s_warp, &tile_total);
+    if (warp == 0) {
+        uint64_t excl = 0;
+        if (tile == 0) {
+            if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
+        } else {
+            if (lane == 0) st_release(status + tile, make_status(epoch, ST_AGGREGATE, tile_total));
+            excl = look_back(status, (long long)tile, epoch, &hdr->flags);
+            if (lane == 0) st_release(status + tile, make_status(epoch, ST_PREFIX, excl + tile_total));
+        }
+        if (lane == 0) s_tile_excl = excl;
+    }
+    __syncthreads();
+    const uint64_t G0 = s_tile_excl;
+
+    /* 4. encode into the staging buffer */
+    const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
+    uint64_t g = G0 + excl_local;
+    uint64_t cap_first = NONE;
+    Packer pk;
+    pk.start(shift + excl_local);
+    if (__all_sync(FULL_MASK, ascii)) {
+#pragma unroll
+        for (int k = 0; k < UPT; k++) {
+            if ((inr >> k) & 1) {
+                const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFF;
+                if (g >= cap && cap_first == NONE) cap_first = e0 + k - head;
+                pk.put(stage, u, 1);
+                g++;
+            }
+        }
+    } else {
+        uint32_t prev = pu;
+#pragma unroll
+        for (int k = 0; k < UPT; k++) {
+            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
+            if ((inr >> k) & 1) {
+                int len;
+                const uint32_t v = encode_unit(u, prev, &len);
+                /* a character starts here unless u is the low half of a pair;
+                 * a pair needs its 4 bytes to fit */
+                const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
+                const bool pair_tail = is_low(u) && is_high(prev);
+                const uint32_t need = (is_high(u) && is_low(next)) ? 4 : len;
+                if (!pair_tail && g + need > cap && cap_first == NONE) cap_first = e0 + k - head;
+                pk.put(stage, v, len);
+                g += len;
+            }
+            prev = u;
+        }
+    }
+    pk.finish(stage);
+
+    /* 5. first error and first character that does not fit */
+    if (__syncthreads_or(first_err != NONE)) {
+        const uint64_t m = block_min<THREADS>(first_err, s_min);
+        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
+    }
+    if (G0 <= cap && G0 + tile_total > cap) {
+        const uint64_t m = block_min<THREADS>(cap_first, s_min);
+        if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
+    }
+    __syncthreads();
+
+    /* write the tile's output bytes [G0, G0 + cnt), clipped to the capacity */
+    const uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
+    uint8_t *gbase = out + G0 - shift;
+    const uint8_t *sbytes = reinterpret_cast<const uint8_t *>(stage);
+    const uint32_t lim = shift + (uint32_t)cnt;
+    const uint32_t nvec = (lim + 15) / 16;
+    for (uint32_t i = tid; i < nvec; i += THREADS) {
+        const uint32_t lo = 16 * i, hi = lo + 16;
+        if (lo >= shift && hi <= lim) {
+            st_stream16(gbase + lo, s_stage4[i]);
+        } else {
+            for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = sbytes[b];
+        }
+    }
+
+    /* the CTA that finishes last writes the result */
+    if (!finish_cta(hdr, &s_flag)) return;
+    const uint64_t f = ld_relaxed(&hdr->err_pos);
+    const uint64_t cpos = ld_relaxed(&hdr->cap_pos);
+    const unsigned flags = *(volatile unsigned *)&hdr->flags;
+    int32_t error = GPUTF_E_OK;
+    uint64_t pos = n;
+    if (flags & FLAG_TIMEOUT) {
+        error = GPUTF_E_TIMEOUT;
+        pos = 0;
+    } else if (cpos != NONE && (f == NONE || cpos < f)) {
+        error = GPUTF_E_OUTPUT_TOO_SMALL;
+        pos = cpos;
+    } else if (f != NONE) {
+        error = GPUTF_E_SURROGATE;
+        pos = f;
+    }
+    uint64_t written = 0;
+    if (error == GPUTF_E_OK) {
+        written = ld_relaxed(status + gridDim.x - 1) & VALUE_MASK;
+    } else if (error != GPUTF_E_TIMEOUT) {
+        const uint64_t t = (head + pos) / TILE;
+        const uint64_t before = t ? (ld_relaxed(status + t - 1) & VALUE_MASK) : 0;
+        const uint64_t start = t * TILE > head ? t * TILE - head : 0;
+        uint32_t c = 0;
+        for (uint64_t i = start + tid; i < pos; i += THREADS) {
+            const uint32_t u = in[i];
+            c += u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
+        }
+        uint32_t sum;
+        block_exclusive<THREADS>(c, s_warp, &sum);
+        written = before + sum;
+    }
+    if (tid == 0) {
+        res->error = error;
+        res->reserved = 0;
+        res->position = pos;
+        res->written = written;
+    }
+    reset_workspace(hdr, status, status_words);
+}
+
+/* ------------------------------------------------------------------------
+ * Validate-only and length-only passes.
+ * ---------------------------------------------------------------------- */
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
+                      DevResult *res)
+{
+    constexpr int UPT = 2 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    __shared__ unsigned long long s_min[THREADS / 32];
+    __shared__ unsigned s_flag;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t head = ((uintptr_t)in & 15) / 2;
+    const uint16_t *base = in - head;
+    const uint64_t endx = head + n;
+    uint64_t first_err = NONE;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
+        uint32_t w[WORDS];
+        load_chunk16<WORDS>(base, e0, head, endx, w);
+        bool sur = false;
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) sur |= has_surrogate(w[k]);
+        uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
+        uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
+        if (lane == 0) pu = unit_at(base, (long long)e0 - 1, head, endx);
+        if (lane == 31) nu = unit_at(base, (long long)(e0 + UPT), head, endx);
+        if (sur && first_err == NONE) {
+            uint32_t prev = pu;
+#pragma unroll
+            for (int k = 0; k < UPT; k++) {
+                const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
+                const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
+                const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
+                const long long ex = (long long)(e0 + k);
+                if (bad && ex >= (long long)head && ex < (long long)endx && first_err == NONE)
+                    first_err = e0 + k - head;
+                prev = u;
+            }
+        }
+        if (__syncthreads_or(first_err != NONE)) break;
+    }
+    if (__syncthreads_or(first_err != NONE)) {
+        const uint64_t m = block_min<THREADS>(first_err, s_min);
+        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
+    }
+    if (!finish_cta(hdr, &s_flag)) return;
+    if (tid == 0) {
+        const uint64_t f = ld_relaxed(&hdr->err_pos);
+        res->error = f == NONE ? GPUTF_E_OK : GPUTF_E_SURROGATE;
+        res->reserved = 0;
+        res->position = f == NONE ? n : f;
+        res->written = 0;
+    }
+    reset_workspace(hdr, nullptr, 0);
+}
+
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles,
+                              WsHeader *hdr, unsigned long long *len_out)
+{
+    constexpr int UPT = 2 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    __shared__ uint32_t s_warp[THREADS / 32 + 1];
+    __shared__ unsigned s_flag;
+    const int tid = threadIdx.x;
+    const uint64_t head = ((uintptr_t)in & 15) / 2;
+    const uint16_t *base = in - head;
+    const uint64_t endx = head + n;
+    uint32_t acc = 0;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
+        uint32_t w[WORDS];
+        const bool interior = load_chunk16<WORDS>(base, e0, head, endx, w);
+#pragma unroll
+        for (int k = 0; k < UPT; k++) {
+            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
+            const long long ex = (long long)(e0 + k);
+            const bool in_range = interior || (ex >= (long long)head && ex < (long long)endx);
+            const uint32_t l = u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
+            acc += in_range ? l : 0;
+        }
+    }
+    uint32_t sum;
+    block_exclusive<THREADS>(acc, s_warp, &sum);
+    if (tid == 0) atomicAdd(&hdr->accum, (unsigned long long)sum);
+    if (!finish_cta(hdr, &s_flag)) return;
+    if (tid == 0) *len_out = ld_relaxed(&hdr->accum);
+    reset_workspace(hdr, nullptr, 0);
+}
+
+/* ------------------------------------------------------------------------
+ * Launchers.
+ * ---------------------------------------------------------------------- */
+constexpr int U16_THREADS = 256;
+constexpr int U16_WORDS = 8;    /* 16 units per thread, 4096-unit tiles */
+constexpr uint64_t U16_TILE = (uint64_t)U16_THREADS * 2 * U16_WORDS;
+
+uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
+{
+    return (((uintptr_t)in % 16) / 2 + n + U16_TILE) / U16_TILE;   /* at least one tile */
+}
+
+cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res,
+                                 cudaStream_t stream)
+{
+    const uint64_t tiles = utf16_to_utf8_tiles(in, n);
+    const size_t smem = ((3 * U16_TILE + 16) / 4) * 4;
+    WsHeader *hdr = static_cast<WsHeader *>(ws);
+    auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
+    utf16_to_utf8_kernel<U16_THREADS, U16_WORDS><<<(unsigned)tiles, U16_THREADS, smem, stream>>>(
+        in, n, out, cap, hdr, status, status_words, res);
+    return cudaGetLastError();
+}
+
+static unsigned pass_grid16(uint64_t tiles, int sms)
+{
+    uint64_t g = (uint64_t)sms * 8;
+    return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
+}
+
+cudaError_t launch_validate_utf16(const uint16_t *in, uint64_t n, void *ws, DevResult *res,
+                                  int sms, cudaStream_t stream)
+{
+    constexpr int T = 256, W = 8;
+    constexpr uint64_t TILE = (uint64_t)T * 2 * W;
+    const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
+    validate_utf16_kernel<T, W><<<pass_grid16(tiles, sms), T, 0, stream>>>(
+        in, n, tiles, static_cast<WsHeader *>(ws), res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *ws,
+                                          unsigned long long *len, int sms, cudaStream_t stream)
+{
+    constexpr int T = 256, W = 8;
+    constexpr uint64_t TILE = (uint64_t)T * 2 * W;
+    const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
+    utf8_length_from_utf16_kernel<T, W><<<pass_grid16(tiles, sms), T, 0, stream>>>(
+        in, n, tiles, static_cast<WsHeader *>(ws), len);
+    return cudaGetLastError();
+}
+
+}  // namespace gputf

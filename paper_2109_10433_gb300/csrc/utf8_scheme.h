@@ -1,0 +1,219 @@
+/*
+ * Per-byte UTF-8 validation with three 16-entry nibble tables, four bytes at
+ * a time, plus the scalar decoder that pins the exact error class and start.
+ *
+ * The same source compiles for the GPU (nvcc) and for the host (gcc), so the
+ * host test suite can prove the scheme exhaustively on short strings.
+ *
+ * Scheme (validation rules 1-6 of Section 3 of the paper, as pair terms):
+ *   for byte c with previous byte p,
+ *     E = T1[p >> 4] & T2[p & 15] & T3[c >> 4]          (tables: utf8_tables.h)
+ *   c is flagged when a bit of E other than TWO_CONTS is set, or when the
+ *   TWO_CONTS bit (p and c both continuation bytes) differs from "a lead of
+ *   three or four bytes sits two or three bytes before c" (must23).
+ * The end of the input is checked by running one zero byte past it: a
+ * character cut short there is flagged at the end position n.
+ *
+ * The flags are not the error report: the first flagged position f lies in
+ * [s, s + 3] where s is the start of the first invalid character, and the
+ * scalar step gputf_utf8_fixup() walks forward from just before f to find s
+ * and the class, in decoding order.
+ *
+ * Lookups use PRMT: a 16-entry byte table is two 8-byte halves; a selector
+ * nibble with bit 3 set selects "replicate the sign bit", which also gives a
+ * cheap per-byte mask of "index >= 8".
+ */
+#ifndef GPUTF_UTF8_SCHEME_H
+#define GPUTF_UTF8_SCHEME_H
+
+#include <stdint.h>
+#include "utf8_tables.h"
+
+#if defined(__CUDACC__)
+#define GPUTF_HD static __host__ __device__ __forceinline__
+#else
+#define GPUTF_HD static inline
+#endif
+
+/* Error classes of the public interface. */
+#define GPUTF_E_OK 0
+#define GPUTF_E_HEADER_BITS 1
+#define GPUTF_E_TOO_SHORT 2
+#define GPUTF_E_TOO_LONG 3
+#define GPUTF_E_OVERLONG 4
+#define GPUTF_E_TOO_LARGE 5
+#define GPUTF_E_SURROGATE 6
+#define GPUTF_E_OUTPUT_TOO_SMALL 7
+#define GPUTF_E_TIMEOUT 8
+#define GPUTF_E_INTERNAL 9
+
+/* PTX prmt.b32 default mode: result byte k is byte (sel_k & 7) of {b:a}
+ * (a = bytes 0-3, b = bytes 4-7); if sel_k & 8 the sign bit of that byte is
+ * replicated instead.  sel_k is bits 4k..4k+3 of sel. */
+GPUTF_HD uint32_t gputf_prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+#else
+    uint64_t v = (uint64_t)a | ((uint64_t)b << 32);
+    uint32_t d = 0;
+    for (int k = 0; k < 4; k++) {
+        uint32_t s = (sel >> (4 * k)) & 0xF;
+        uint32_t byte = (uint32_t)(v >> (8 * (s & 7))) & 0xFF;
+        if (s & 8) byte = (byte & 0x80) ? 0xFF : 0x00;
+        d |= byte << (8 * k);
+    }
+    return d;
+#endif
+}
+
+/* High 32 bits of (hi:lo) << s, 0 < s < 32. */
+GPUTF_HD uint32_t gputf_fshl(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_l(lo, hi, s);
+#else
+    return (hi << s) | (lo >> (32 - s));
+#endif
+}
+
+/* Low 32 bits of (hi:lo) >> s, 0 <= s < 32. */
+GPUTF_HD uint32_t gputf_fshr(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(lo, hi, s);
+#else
+    return s ? (lo >> s) | (hi << (32 - s)) : lo;
+#endif
+}
+
+/* Pack the four nibbles held in the low halves of the bytes of x into a
+ * 16-bit PRMT selector (nibble k = byte k). */
+GPUTF_HD uint32_t gputf_pack_nibbles(uint32_t x)
+{
+    uint32_t y = x | (x >> 4);
+    return gputf_prmt(y, 0, 0x0020);
+}
+
+/* 16-entry table lookup: sel = packed indexes, m = 0xFF in each byte whose
+ * index is >= 8. */
+GPUTF_HD uint32_t gputf_lut16(uint32_t sel, uint32_t m, uint32_t q0, uint32_t q1,
+                              uint32_t q2, uint32_t q3)
+{
+    uint32_t lo = gputf_prmt(q0, q1, sel);
+    uint32_t hi = gputf_prmt(q2, q3, sel ^ 0x8888);
+    return (hi & m) | (lo & ~m);
+}
+
+/* Error flags of the four bytes of w (nonzero byte k: byte k of w flagged),
+ * given p, the four bytes just before w. */
+GPUTF_HD uint32_t gputf_utf8_errors(uint32_t p, uint32_t w)
+{
+    uint32_t prev1 = gputf_fshl(p, w, 8);     /* byte k: the byte before w.k   */
+    uint32_t prev2 = gputf_fshl(p, w, 16);    /* byte k: two bytes before w.k  */
+    uint32_t prev3 = gputf_fshl(p, w, 24);    /* byte k: three bytes before    */
+
+    uint32_t sel_p_hi = gputf_pack_nibbles((prev1 >> 4) & 0x0F0F0F0Fu);
+    uint32_t sel_p_lo = gputf_pack_nibbles(prev1 & 0x0F0F0F0Fu);
+    uint32_t sel_c_hi = gputf_pack_nibbles((w >> 4) & 0x0F0F0F0Fu);
+    uint32_t m_p_hi = gputf_prmt(prev1, 0, 0xBA98);        /* p >> 4 >= 8  */
+    uint32_t m_p_lo = gputf_prmt(prev1 << 4, 0, 0xBA98);   /* p & 15 >= 8  */
+    uint32_t m_c_hi = gputf_prmt(w, 0, 0xBA98);            /* c >> 4 >= 8  */
+
+    uint32_t e = gputf_lut16(sel_p_hi, m_p_hi, GPUTF_T1_W0, GPUTF_T1_W1, GPUTF_T1_W2, GPUTF_T1_W3)
+               & gputf_lut16(sel_p_lo, m_p_lo, GPUTF_T2_W0, GPUTF_T2_W1, GPUTF_T2_W2, GPUTF_T2_W3)
+               & gputf_lut16(sel_c_hi, m_c_hi, GPUTF_T3_W0, GPUTF_T3_W1, GPUTF_T3_W2, GPUTF_T3_W3);
+
+    /* bit 7 of each byte: byte two back >= 0xE0, or three back >= 0xF0 */
+    uint32_t ge_e0 = prev2 & (prev2 << 1) & (prev2 << 2);
+    uint32_t ge_f0 = prev3 & (prev3 << 1) & (prev3 << 2) & (prev3 << 3);
+    uint32_t must23 = (ge_e0 | ge_f0) & 0x80808080u;
+
+    return (e & 0x7F7F7F7Fu) | ((e ^ must23) & 0x80808080u);
+}
+
+/* Bit 7 of each byte set iff that byte of x is nonzero. */
+GPUTF_HD uint32_t gputf_nonzero_bytes(uint32_t x)
+{
+    return (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
+/* One UTF-8 character at in[p], p < n: returns its class and, when valid,
+ * its length.  Classes in decoding order: the lead byte (stray continuation,
+ * or 0xF8..0xFF), then missing continuation bytes, then the ranges of the
+ * second byte that give overlong, too large and surrogate values. */
+GPUTF_HD int gputf_utf8_char(const uint8_t *in, uint64_t n, uint64_t p, int *len)
+{
+    uint32_t b = in[p];
+    if (b < 0x80) {
+        *len = 1;
+        return GPUTF_E_OK;
+    }
+    if (b < 0xC0) return GPUTF_E_TOO_LONG;
+    if (b >= 0xF8) return GPUTF_E_HEADER_BITS;
+    int L = b >= 0xF0 ? 4 : (b >= 0xE0 ? 3 : 2);
+    for (int k = 1; k < L; k++) {
+        if (p + (uint64_t)k >= n || (in[p + k] & 0xC0) != 0x80) return GPUTF_E_TOO_SHORT;
+    }
+    uint32_t b1 = in[p + 1];
+    if (L == 2 && b < 0xC2) return GPUTF_E_OVERLONG;
+    if (L == 3 && b == 0xE0 && b1 < 0xA0) return GPUTF_E_OVERLONG;
+    if (L == 3 && b == 0xED && b1 >= 0xA0) return GPUTF_E_SURROGATE;
+    if (L == 4 && b == 0xF0 && b1 < 0x90) return GPUTF_E_OVERLONG;
+    if (L == 4 && (b > 0xF4 || (b == 0xF4 && b1 >= 0x90))) return GPUTF_E_TOO_LARGE;
+    *len = L;
+    return GPUTF_E_OK;
+}
+
+/* From the first flagged position f (0 <= f <= n, n > 0), find the start and
+ * class of the first invalid character.  The scan starts at most three bytes
+ * before f, backed up over at most four continuation bytes to a character
+ * start of the valid prefix.  Returns 0 when it finds the error, -1 if the
+ * flags and the decoder disagree (which the scheme's proof rules out). */
+GPUTF_HD int gputf_utf8_fixup(const uint8_t *in, uint64_t n, uint64_t f, int *cls,
+                              uint64_t *start)
+{
+    uint64_t q = f >= 3 ? f - 3 : 0;
+    for (int k = 0; k < 4 && q > 0 && (in[q] & 0xC0) == 0x80; k++) q--;
+    uint64_t p = q;
+    for (int it = 0; it < 8 && p < n; it++) {
+        int L = 1;
+        int c = gputf_utf8_char(in, n, p, &L);
+        if (c != GPUTF_E_OK) {
+            *cls = c;
+            *start = p;
+            return 0;
+        }
+        p += (uint64_t)L;
+    }
+    *cls = GPUTF_E_OK;
+    *start = p;
+    return -1;
+}
+
+#if !defined(__CUDACC__)
+/* Host-side mirror of what the kernels compute over a whole buffer: the first
+ * flagged position (<= n), or UINT64_MAX when nothing is flagged.  Bytes
+ * before the buffer and from n on read as zero. */
+GPUTF_HD uint64_t gputf_utf8_first_flag(const uint8_t *in, uint64_t n)
+{
+    uint32_t p = 0;
+    for (uint64_t base = 0; base <= n; base += 4) {
+        uint32_t w = 0;
+        for (int k = 0; k < 4; k++)
+            if (base + k < n) w |= (uint32_t)in[base + k] << (8 * k);
+        uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(p, w));
+        while (nz) {
+            int k = (int)((__builtin_ctz(nz) - 7) / 8);
+            if (base + (uint64_t)k <= n) return base + (uint64_t)k;
+            nz &= nz - 1;
+        }
+        p = w;
+    }
+    return UINT64_MAX;
+}
+#endif
+
+#endif

@@ -1,0 +1,455 @@
+/*
+ * Validating UTF-8 -> UTF-16LE, and the UTF-8 validate-only and length-only
+ * passes.
+ *
+ * One CTA transcodes one tile of TILE input bytes (tiles in ticket order):
+ *   1. load: each thread reads BPT consecutive bytes with 16-byte loads (the
+ *      tile grid is aligned to 16 bytes below the input pointer, so every
+ *      load is aligned; the first and last chunk of the buffer are read byte
+ *      by byte), plus the 4 bytes before its chunk and the 4 after, taken
+ *      from the neighbouring lanes or, at warp edges, from memory;
+ *   2. classify and validate: a warp whose bytes (and the bytes just before)
+ *      are all ASCII skips validation (the all-ASCII fast path of
+ *      Algorithm 3); other threads run the nibble-table scheme of
+ *      utf8_scheme.h four bytes at a time;
+ *   3. per-byte output length: 1 unit at every byte that is not a
+ *      continuation byte, 2 at a four-byte lead (Table 2: supplementary
+ *      characters take a surrogate pair), summed per thread, scanned over the
+ *      block and over all earlier tiles by decoupled look-back;
+ *   4. decode at every lead with the bit arithmetic of Section 3 and Figs.
+ *      2-4 (payload bits of the lead and continuation bytes; for four-byte
+ *      characters subtract 0x10000 and split into 110110 / 110111 halves),
+ *      into a shared-memory staging buffer placed so that it shares the
+ *      output's alignment, then write the tile's output range with aligned
+ *      16-byte stores;
+ *   5. the first flagged byte goes to an atomicMin; the CTA that finishes
+ *      last turns it into the exact error start and class (scalar step of
+ *      utf8_scheme.h), the output count of the valid prefix and the result.
+ * Output past the caller's capacity is never written; the first character
+ * that does not fit is reported as GPUTF_OUTPUT_TOO_SMALL.
+ */
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gputf {
+
+/* One byte at extended index ex (input index ex - head), zero outside. */
+__device__ __forceinline__ uint32_t byte_at(const uint8_t *base, long long ex, uint64_t head,
+                                            uint64_t endx)
+{
+    return (ex >= (long long)head && ex < (long long)endx) ? base[ex] : 0u;
+}
+
+/* Four bytes at extended index ex (a multiple of 4), zero outside. */
+__device__ __forceinline__ uint32_t word_at(const uint8_t *base, long long ex, uint64_t head,
+                                            uint64_t endx)
+{
+    if (ex >= (long long)head && ex + 4 <= (long long)endx)
+        return *reinterpret_cast<const uint32_t *>(base + ex);
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) w |= byte_at(base, ex + k, head, endx) << (8 * k);
+    return w;
+}
+
+/* Loads one thread's chunk of 4*WORDS bytes; returns true when it lies
+ * wholly inside the input. */
+template <int WORDS>
+__device__ __forceinline__ bool load_chunk8(const uint8_t *base, uint64_t e0, uint64_t head,
+                                            uint64_t endx, uint32_t (&w)[WORDS])
+{
+    const bool interior = e0 >= head && e0 + 4 * WORDS <= endx;
+    if (interior) {
+#pragma unroll
+        for (int v = 0; v < WORDS / 4; v++) {
+            uint4 q = ld_stream16(base + e0 + 16 * v);
+            w[4 * v + 0] = q.x;
+            w[4 * v + 1] = q.y;
+            w[4 * v + 2] = q.z;
+            w[4 * v + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = word_at(base, (long long)(e0 + 4 * k), head, endx);
+    }
+    return interior;
+}
+
+/* Bit 7 of each byte of the word at extended index ex: set when the byte is
+ * an input byte (head <= index < endx). */
+__device__ __forceinline__ uint32_t range_mask(long long ex, uint64_t head, uint64_t endx, bool incl_end)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        long long e = ex + k;
+        bool in = e >= (long long)head && (incl_end ? e <= (long long)endx : e < (long long)endx);
+        m |= in ? (0x80u << (8 * k)) : 0u;
+    }
+    return m;
+}
+
+/* Byte index (0..3) of the lowest byte with bit 7 set in a nonzero mask. */
+__device__ __forceinline__ int first_byte(uint32_t m) { return (__ffs(m) - 8) >> 3; }
+
+/* UTF-16 of the character whose lead is byte 0 of q (bytes 1..3 follow).
+ * Returns the unit count; *u0 and *u1 get the units. */
+__device__ __forceinline__ int decode_utf8(uint32_t q, uint32_t *u0, uint32_t *u1)
+{
+    const uint32_t b0 = q & 0xFF;
+    const uint32_t two = ((b0 & 0x1F) << 6) | ((q >> 8) & 0x3F);
+    const uint32_t three = ((b0 & 0x0F) << 12) | ((q >> 2) & 0x0FC0) | ((q >> 16) & 0x3F);
+    const uint32_t four = ((b0 & 0x07) << 18) | ((q << 4) & 0x3F000) | ((q >> 10) & 0x0FC0) |
+                          ((q >> 24) & 0x3F);
+    const uint32_t x = four - 0x10000;
+    uint32_t u = b0 < 0x80 ? b0 : (b0 < 0xE0 ? two : three);
+    const bool pair = b0 >= 0xF0;
+    *u0 = pair ? (0xD800 | ((x >> 10) & 0x3FF)) : u;
+    *u1 = 0xDC00 | (x & 0x3FF);
+    return pair ? 2 : 1;
+}
+
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
+                     uint64_t cap, WsHeader *hdr, unsigned long long *status,
+                     uint64_t status_words, DevResult *res)
+{
+    constexpr int BPT = 4 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    constexpr int WARPS = THREADS / 32;
+    __shared__ uint32_t s_warp[WARPS + 1];
+    __shared__ unsigned long long s_min[WARPS];
+    __shared__ unsigned long long s_tile_excl;
+    __shared__ unsigned s_tile, s_flag;
+    extern __shared__ uint4 s_stage4[];
+    uint16_t *stage = reinterpret_cast<uint16_t *>(s_stage4);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = (unsigned)atomicAdd(&hdr->ticket, 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
+
+    const uint64_t head = (uintptr_t)in & 15;
+    const uint8_t *base = in - head;
+    const uint64_t endx = head + n;    /* extended index of the end position */
+    const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
+
+    /* 1. load */
+    uint32_t w[WORDS];
+    const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
+    uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
+    uint32_t nw = __shfl_down_sync(FULL_MASK, w[0], 1);
+    if (lane == 0) pw = word_at(base, (long long)e0 - 4, head, endx);
+    if (lane == 31) nw = word_at(base, (long long)(e0 + BPT), head, endx);
+
+    /* 3. per-byte lengths: leads (non-continuation bytes) and four-byte leads */
+    uint32_t lead[WORDS], f4[WORDS];
+    uint32_t any = pw, total = 0;
+#pragma unroll
+    for (int k = 0; k < WORDS; k++) {
+        const uint32_t x = w[k];
+        any |= x;
+        lead[k] = ~(x & ~(x << 1)) & 0x80808080u;
+        f4[k] = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
+        if (!interior) {
+            const uint32_t rm = range_mask((long long)(e0 + 4 * k), head, endx, false);
+            lead[k] &= rm;
+            f4[k] &= rm;
+        }
+        total += __popc(lead[k]) + __popc(f4[k]);
+    }
+
+    /* 2. validation, skipped by all-ASCII warps and all-ASCII threads */
+    const bool ascii = (any & 0x80808080u) == 0;
+    uint64_t first_err = NONE;
+    if (!__all_sync(FULL_MASK, ascii) && !ascii) {
+#pragma unroll
+        for (int k = WORDS - 1; k >= 0; k--) {
+            uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
+            if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
+            if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
+        }
+    }
+
+    /* block scan and look-back */
+    uint32_t tile_total;
+    const uint32_t excl_local = block_exclusive<THREADS>(total, s_warp, &tile_total);
+    if (warp == 0) {
+        uint64_t excl = 0;
+        if (tile == 0) {
+            if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
+        } else {
+            if (lane == 0) st_release(status + tile, make_status(epoch, ST_AGGREGATE, tile_total));
+            excl = look_back(status, (long long)tile, epoch, &hdr->flags);
+            if (lane == 0) st_release(status + tile, make_status(epoch, ST_PREFIX, excl + tile_total));
+        }
+        if (lane == 0) s_tile_excl = excl;
+    }
+    __syncthreads();
+    const uint64_t G0 = s_tile_excl;
+
+    /* 4. decode into the staging buffer */
+    const uint32_t shift = (uint32_t)(((uintptr_t)(out + G0) >> 1) & 7);
+    uint32_t o = shift + excl_local;
+    uint64_t g = G0 + excl_local;
+    uint64_t cap_first = NONE;
+    if (__all_sync(FULL_MASK, ascii)) {
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (lead[k] & (0x80u << (8 * j))) {
+                    stage[o] = (uint16_t)((w[k] >> (8 * j)) & 0xFF);
+                    if (g >= cap && cap_first == NONE) cap_first = e0 + 4 * k + j - head;
+                    o++;
+                    g++;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) {
+            const uint32_t nxt = k + 1 < WORDS ? w[k + 1] : nw;
+            uint32_t m = lead[k];
+            while (m) {
+                const int j = first_byte(m);
+                m &= m - 1;
+                const uint32_t q = gputf_fshr(w[k], nxt, 8 * j);
+                uint32_t u0, u1;
+                const int c = decode_utf8(q, &u0, &u1);
+                stage[o] = (uint16_t)u0;
+                if (c == 2) stage[o + 1] = (uint16_t)u1;
+                if (g + c > cap && cap_first == NONE) cap_first = e0 + 4 * k + j - head;
+                o += c;
+                g += c;
+            }
+        }
+    }
+
+    /* 5. first error and first character that does not fit */
+    if (__syncthreads_or(first_err != NONE)) {
+        const uint64_t m = block_min<THREADS>(first_err, s_min);
+        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
+    }
+    if (G0 <= cap && G0 + tile_total > cap) {
+        const uint64_t m = block_min<THREADS>(cap_first, s_min);
+        if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
+    }
+    __syncthreads();
+
+    /* write the tile's output range [G0, G0 + cnt), clipped to the capacity */
+    uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
+    uint16_t *gbase = out + G0 - shift;     /* 16-byte aligned; index 0 <-> stage[0] */
+    const uint32_t lim = shift + (uint32_t)cnt;
+    const uint32_t nvec = (lim + 7) / 8;
+    for (uint32_t i = tid; i < nvec; i += THREADS) {
+        const uint32_t lo = 8 * i, hi = lo + 8;
+        if (lo >= shift && hi <= lim) {
+            st_stream16(gbase + lo, s_stage4[i]);
+        } else {
+            for (uint32_t u = lo < shift ? shift : lo; u < (hi < lim ? hi : lim); u++) gbase[u] = stage[u];
+        }
+    }
+
+    /* the CTA that finishes last writes the result */
+    if (!finish_cta(hdr, &s_flag)) return;
+    const uint64_t f = ld_relaxed(&hdr->err_pos);
+    const uint64_t cpos = ld_relaxed(&hdr->cap_pos);
+    const unsigned flags = *(volatile unsigned *)&hdr->flags;
+    int32_t error = GPUTF_E_OK;
+    uint64_t pos = n;
+    if (flags & FLAG_TIMEOUT) {
+        error = GPUTF_E_TIMEOUT;
+        pos = 0;
+    } else {
+        uint64_t s = NONE;
+        int cls = GPUTF_E_OK;
+        if (f != NONE) {
+            if (gputf_utf8_fixup(in, n, f, &cls, &s) != 0) cls = GPUTF_E_INTERNAL;
+        }
+        if (cpos != NONE && (s == NONE || cpos < s)) {
+            error = GPUTF_E_OUTPUT_TOO_SMALL;
+            pos = cpos;
+        } else if (s != NONE) {
+            error = cls;
+            pos = s;
+        }
+    }
+    uint64_t written = 0;
+    if (error == GPUTF_E_OK) {
+        written = ld_relaxed(status + gridDim.x - 1) & VALUE_MASK;
+    } else if (error != GPUTF_E_TIMEOUT) {
+        /* output units of [0, pos): earlier tiles' total plus a recount */
+        const uint64_t t = (head + pos) / TILE;
+        const uint64_t before = t ? (ld_relaxed(status + t - 1) & VALUE_MASK) : 0;
+        const uint64_t start = t * TILE > head ? t * TILE - head : 0;
+        uint32_t c = 0;
+        for (uint64_t i = start + tid; i < pos; i += THREADS) {
+            const uint32_t b = in[i];
+            c += ((b & 0xC0) != 0x80) + (b >= 0xF0);
+        }
+        uint32_t sum;
+        block_exclusive<THREADS>(c, s_warp, &sum);
+        written = before + sum;
+    }
+    if (tid == 0) {
+        res->error = error;
+        res->reserved = 0;
+        res->position = pos;
+        res->written = written;
+    }
+    reset_workspace(hdr, status, status_words);
+}
+
+/* ------------------------------------------------------------------------
+ * Validate-only and length-only passes: one read of the input, no scan.
+ * ---------------------------------------------------------------------- */
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
+                     DevResult *res)
+{
+    constexpr int BPT = 4 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    __shared__ unsigned long long s_min[THREADS / 32];
+    __shared__ unsigned s_flag;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t head = (uintptr_t)in & 15;
+    const uint8_t *base = in - head;
+    const uint64_t endx = head + n;
+    uint64_t first_err = NONE;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
+        uint32_t w[WORDS];
+        const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
+        uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
+        if (lane == 0) pw = word_at(base, (long long)e0 - 4, head, endx);
+        uint32_t any = pw;
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) any |= w[k];
+        if ((any & 0x80808080u) != 0 && first_err == NONE) {
+#pragma unroll
+            for (int k = WORDS - 1; k >= 0; k--) {
+                uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
+                if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
+                if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
+            }
+        }
+        if (__syncthreads_or(first_err != NONE)) break;   /* later tiles cannot hold an earlier error */
+    }
+    if (__syncthreads_or(first_err != NONE)) {
+        const uint64_t m = block_min<THREADS>(first_err, s_min);
+        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
+    }
+    if (!finish_cta(hdr, &s_flag)) return;
+    if (tid == 0) {
+        const uint64_t f = ld_relaxed(&hdr->err_pos);
+        int cls = GPUTF_E_OK;
+        uint64_t s = n;
+        if (f != NONE && gputf_utf8_fixup(in, n, f, &cls, &s) != 0) cls = GPUTF_E_INTERNAL;
+        res->error = cls;
+        res->reserved = 0;
+        res->position = s;
+        res->written = 0;
+    }
+    reset_workspace(hdr, nullptr, 0);
+}
+
+template <int THREADS, int WORDS>
+__global__ void __launch_bounds__(THREADS)
+utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
+                              WsHeader *hdr, unsigned long long *len_out)
+{
+    constexpr int BPT = 4 * WORDS;
+    constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    __shared__ uint32_t s_warp[THREADS / 32 + 1];
+    __shared__ unsigned s_flag;
+    const int tid = threadIdx.x;
+    const uint64_t head = (uintptr_t)in & 15;
+    const uint8_t *base = in - head;
+    const uint64_t endx = head + n;
+    uint64_t acc = 0;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
+        uint32_t w[WORDS];
+        const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) {
+            const uint32_t x = w[k];
+            uint32_t lead = ~(x & ~(x << 1)) & 0x80808080u;
+            uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
+            if (!interior) {
+                const uint32_t rm = range_mask((long long)(e0 + 4 * k), head, endx, false);
+                lead &= rm;
+                f4 &= rm;
+            }
+            acc += __popc(lead) + __popc(f4);
+        }
+    }
+    /* per-thread counts stay below 2^32 for one CTA's share of any input */
+    uint32_t sum;
+    block_exclusive<THREADS>((uint32_t)acc, s_warp, &sum);
+    if (tid == 0) atomicAdd(&hdr->accum, (unsigned long long)sum);
+    if (!finish_cta(hdr, &s_flag)) return;
+    if (tid == 0) *len_out = ld_relaxed(&hdr->accum);
+    reset_workspace(hdr, nullptr, 0);
+}
+
+/* ------------------------------------------------------------------------
+ * Launchers.
+ * ---------------------------------------------------------------------- */
+constexpr int U8_THREADS = 256;
+constexpr int U8_WORDS = 4;     /* 16 bytes per thread, 4 KiB tiles */
+constexpr uint64_t U8_TILE = (uint64_t)U8_THREADS * 4 * U8_WORDS;
+
+uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
+{
+    return ((uintptr_t)in % 16 + n + 1 + U8_TILE - 1) / U8_TILE;
+}
+
+cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res,
+                                 cudaStream_t stream)
+{
+    const uint64_t tiles = utf8_to_utf16_tiles(in, n);
+    const size_t smem = (2 * U8_TILE + 8) * sizeof(uint16_t);
+    WsHeader *hdr = static_cast<WsHeader *>(ws);
+    auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
+    utf8_to_utf16_kernel<U8_THREADS, U8_WORDS><<<(unsigned)tiles, U8_THREADS, smem, stream>>>(
+        in, n, out, cap, hdr, status, status_words, res);
+    return cudaGetLastError();
+}
+
+static unsigned pass_grid(uint64_t tiles, int device_sms)
+{
+    uint64_t g = (uint64_t)device_sms * 8;
+    return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
+}
+
+cudaError_t launch_validate_utf8(const uint8_t *in, uint64_t n, void *ws, DevResult *res,
+                                 int sms, cudaStream_t stream)
+{
+    constexpr int T = 256, W = 8;
+    constexpr uint64_t TILE = (uint64_t)T * 4 * W;
+    const uint64_t tiles = ((uintptr_t)in % 16 + n + 1 + TILE - 1) / TILE;
+    validate_utf8_kernel<T, W><<<pass_grid(tiles, sms), T, 0, stream>>>(
+        in, n, tiles, static_cast<WsHeader *>(ws), res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_utf16_length_from_utf8(const uint8_t *in, uint64_t n, void *ws,
+                                          unsigned long long *len, int sms, cudaStream_t stream)
+{
+    constexpr int T = 256, W = 8;
+    constexpr uint64_t TILE = (uint64_t)T * 4 * W;
+    const uint64_t tiles = ((uintptr_t)in % 16 + n + TILE - 1) / TILE;
+    utf16_length_from_utf8_kernel<T, W><<<pass_grid(tiles, sms), T, 0, stream>>>(
+        in, n, tiles, static_cast<WsHeader *>(ws), len);
+    return cudaGetLastError();
+}
+
+}  // namespace gputf

@@ -1,0 +1,280 @@
+"""GPU parity: every call through the C ABI against the CPU oracle, bit for bit
+(output units, error class, error position, units written, lengths).
+
+Covers empty and ragged sizes, sizes around tile boundaries, unaligned input
+and output pointers, every error class at offsets around tile boundaries,
+output capacities that cut the output short, workspace reuse, the host-buffer
+forms, and the benchmark workloads at full size.  Guard bands around every
+output buffer check that nothing is written outside the caller's capacity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE8 = 4096      # input bytes per tile, UTF-8 -> UTF-16
+TILE16 = 4096     # input units per tile, UTF-16 -> UTF-8
+GUARD = 0x5A
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_10433_gb300 as g
+    g.build()
+    return g
+
+
+@pytest.fixture(scope="module")
+def ws(g):
+    return g.Workspace(300 << 20)
+
+
+def dev_u8(a, off=0):
+    buf = torch.zeros(a.size + off + 32, dtype=torch.uint8, device="cuda")
+    if a.size:
+        buf[off:off + a.size] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return buf[off:off + a.size]
+
+
+def dev_u16(a, off=0):
+    buf = torch.zeros(a.size + off + 16, dtype=torch.int16, device="cuda")
+    if a.size:
+        buf[off:off + a.size] = torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).cuda()
+    return buf[off:off + a.size]
+
+
+def check_8to16(g, ws, data, cap=None, in_off=0, out_off=0):
+    data = np.asarray(data, dtype=np.uint8)
+    cap = data.size if cap is None else cap
+    outbuf = torch.full((cap + out_off + 16,), GUARD * 257, dtype=torch.int16, device="cuda")
+    out = outbuf[out_off:out_off + cap]
+    res, _ = g.utf8_to_utf16(dev_u8(data, in_off), out=out, ws=ws)
+    ref, ref_out = oracle.utf8_to_utf16(data, cap=cap)
+    assert tuple(res) == tuple(ref), (res, ref, data.size, cap, in_off, out_off)
+    host = outbuf.cpu().numpy().view(np.uint16)
+    assert np.array_equal(host[out_off:out_off + res.written], ref_out)
+    assert np.all(host[:out_off] == GUARD * 257) and np.all(host[out_off + cap:] == GUARD * 257)
+    return res
+
+
+def check_16to8(g, ws, units, cap=None, in_off=0, out_off=0):
+    units = np.asarray(units, dtype=np.uint16)
+    cap = 3 * units.size if cap is None else cap
+    outbuf = torch.full((cap + out_off + 32,), GUARD, dtype=torch.uint8, device="cuda")
+    out = outbuf[out_off:out_off + cap]
+    res, _ = g.utf16_to_utf8(dev_u16(units, in_off), out=out, ws=ws)
+    ref, ref_out = oracle.utf16_to_utf8(units, cap=cap)
+    assert tuple(res) == tuple(ref), (res, ref, units.size, cap, in_off, out_off)
+    host = outbuf.cpu().numpy()
+    assert np.array_equal(host[out_off:out_off + res.written], ref_out)
+    assert np.all(host[:out_off] == GUARD) and np.all(host[out_off + cap:] == GUARD)
+    return res
+
+
+def check_passes8(g, ws, data, in_off=0):
+    d = dev_u8(np.asarray(data, np.uint8), in_off)
+    assert tuple(g.validate_utf8(d, ws=ws)) == tuple(oracle.validate_utf8(data))
+    assert g.utf16_length_from_utf8(d, ws=ws) == oracle.utf16_length_from_utf8(data)
+
+
+def check_passes16(g, ws, units, in_off=0):
+    d = dev_u16(np.asarray(units, np.uint16), in_off)
+    assert tuple(g.validate_utf16(d, ws=ws)) == tuple(oracle.validate_utf16(units))
+    assert g.utf8_length_from_utf16(d, ws=ws) == oracle.utf8_length_from_utf16(units)
+
+
+MIXES = [W.MIX_LATIN_CYRILLIC, W.MIX_CJK_EMOJI, W.MIX_FOUR_BYTE_HEAVY, W.SCRIPT_MIXED,
+         W.SCRIPT_ASCII, W.SCRIPT_TWO_BYTE, W.SCRIPT_CJK]
+
+
+# ---------------------------------------------------------------------------
+def test_empty(g, ws):
+    for off in (0, 3):
+        check_8to16(g, ws, np.zeros(0, np.uint8), in_off=off)
+        check_16to8(g, ws, np.zeros(0, np.uint16), in_off=off)
+        check_passes8(g, ws, np.zeros(0, np.uint8), in_off=off)
+        check_passes16(g, ws, np.zeros(0, np.uint16), in_off=off)
+
+
+def test_small_sizes_all_mixes(g, ws):
+    rng = np.random.default_rng(1)
+    for n in list(range(1, 80)) + [127, 128, 129, 255, 256, 257, 511, 512, 513, 1000]:
+        mix = MIXES[n % len(MIXES)]
+        d8 = W.utf8_text(n, n, mix)
+        off = int(rng.integers(0, 16))
+        check_8to16(g, ws, d8, in_off=off, out_off=int(rng.integers(0, 8)))
+        check_passes8(g, ws, d8, in_off=off)
+        d16 = W.utf16_text(n, n, mix)
+        off = int(rng.integers(0, 8))
+        check_16to8(g, ws, d16, in_off=off, out_off=int(rng.integers(0, 16)))
+        check_passes16(g, ws, d16, in_off=off)
+
+
+def test_sizes_around_tile_boundaries(g, ws):
+    rng = np.random.default_rng(2)
+    for k in (1, 2, 3, 7):
+        for delta in range(-4, 5):
+            n = k * TILE8 + delta
+            for off in (0, 1, 7, 15):
+                d8 = W.utf8_text(n + off, n, MIXES[(k + delta) % len(MIXES)])
+                check_8to16(g, ws, d8, in_off=off, out_off=int(rng.integers(0, 8)))
+            d16 = W.utf16_text(n, k * TILE16 + delta, MIXES[(k - delta) % len(MIXES)])
+            for off in (0, 1, 5, 7):
+                check_16to8(g, ws, d16, in_off=off, out_off=int(rng.integers(0, 16)))
+            check_passes8(g, ws, d8)
+            check_passes16(g, ws, d16)
+
+
+def test_random_bytes_and_units(g, ws):
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        n = int(rng.integers(1, 20000))
+        b = rng.integers(0, 256, n).astype(np.uint8)
+        if trial % 2:
+            b[: n // 2] &= 0x7F        # a valid ASCII prefix, garbage after
+        check_8to16(g, ws, b)
+        check_passes8(g, ws, b)
+        u = rng.integers(0, 65536, n).astype(np.uint16)
+        u[: n - n // 8] = np.where((u[: n - n // 8] & 0xF800) == 0xD800, 0x41, u[: n - n // 8])
+        check_16to8(g, ws, u)
+        check_passes16(g, ws, u)
+
+
+@pytest.mark.parametrize("kind", W.UTF8_TOKEN_KINDS + ("header",))
+def test_every_utf8_error_class_around_tile_boundaries(g, ws, kind):
+    rng = W.rng_for(17)
+    base = W.utf8_text(5, 3 * TILE8 + 100, W.MIX_FOUR_BYTE_HEAVY)
+    # character starts of the clean text, from CPython's decoding
+    starts = np.cumsum([0] + [len(c.encode()) for c in base.tobytes().decode()])[:-1]
+    near = [s for s in starts if any(abs(int(s) - b) <= 8 for b in (TILE8, 2 * TILE8))]
+    for s in near:
+        tok, cls = W.utf8_error_token(rng, kind)
+        d = np.concatenate([base[:s], np.frombuffer(tok, np.uint8), base[s:]])
+        r = check_8to16(g, ws, d, in_off=int(s) % 16)
+        assert (r.error, r.position) == (cls, int(s))
+        check_passes8(g, ws, d)
+
+
+def test_every_utf16_error_form_around_tile_boundaries(g, ws):
+    rng = W.rng_for(19)
+    base = W.utf16_text(6, 3 * TILE16 + 50, W.MIX_CJK_EMOJI)
+    for pos in list(range(TILE16 - 6, TILE16 + 6)) + list(range(2 * TILE16 - 6, 2 * TILE16 + 6)) + [0, 1, base.size - 1]:
+        tok, _ = W.utf16_error_token(rng)
+        d = np.concatenate([base[:pos], np.array(tok, np.uint16), base[pos:]])
+        check_16to8(g, ws, d, in_off=pos % 8)
+        check_passes16(g, ws, d)
+    # a high surrogate as the very last unit, and a low one as the first
+    check_16to8(g, ws, np.concatenate([base[:TILE16 - 1], [0xD83D]]).astype(np.uint16))
+    check_16to8(g, ws, np.concatenate([[0xDE00], base[:100]]).astype(np.uint16))
+
+
+def test_truncated_tail_at_every_alignment(g, ws):
+    for seq in (b"\xc3", b"\xe9\x8f", b"\xf0\x9f\x98", b"\xe9", b"\xf0", b"\xf0\x9f"):
+        for n in (TILE8 - 3, TILE8 - 2, TILE8 - 1, TILE8, 2 * TILE8 + 1):
+            d = np.concatenate([np.full(n, 0x41, np.uint8), np.frombuffer(seq, np.uint8)])
+            r = check_8to16(g, ws, d)
+            assert r.error == oracle.TOO_SHORT
+            check_passes8(g, ws, d)
+
+
+def test_output_capacity(g, ws):
+    rng = np.random.default_rng(4)
+    for mix in (W.SCRIPT_MIXED, W.MIX_FOUR_BYTE_HEAVY, W.MIX_CJK_EMOJI):
+        d8 = W.utf8_text(7, 5 * TILE8 + 13, mix)
+        d16 = W.utf16_text(8, 5 * TILE16 + 13, mix)
+        need16 = oracle.utf16_length_from_utf8(d8)
+        need8 = oracle.utf8_length_from_utf16(d16)
+        for cap in [0, 1, 2, 3, need16 - 1, need16, need16 + 1] + list(rng.integers(0, need16, 12)):
+            check_8to16(g, ws, d8, cap=int(cap), out_off=int(rng.integers(0, 8)))
+        for cap in [0, 1, 2, 3, 4, need8 - 1, need8, need8 + 1] + list(rng.integers(0, need8, 12)):
+            check_16to8(g, ws, d16, cap=int(cap), out_off=int(rng.integers(0, 16)))
+    # invalid input that would need more than n units: all four-byte leads
+    check_8to16(g, ws, np.full(3 * TILE8 + 5, 0xF0, np.uint8))
+
+
+def test_workspace_reuse_many_calls(g):
+    ws = g.Workspace(1 << 20)
+    rng = np.random.default_rng(5)
+    for i in range(200):
+        n = int(rng.integers(0, 70000))
+        if i % 2:
+            check_8to16(g, ws, W.utf8_text(i, n, MIXES[i % len(MIXES)]))
+        else:
+            check_16to8(g, ws, W.utf16_text(i, n // 2, MIXES[i % len(MIXES)]))
+
+
+def test_host_buffer_forms(g, ws):
+    d8 = W.utf8_text(9, 100000, W.SCRIPT_MIXED)
+    h_in = torch.from_numpy(d8).pin_memory()
+    h_out = torch.empty(d8.size, dtype=torch.int16).pin_memory()
+    d_in = torch.empty(d8.size, dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(d8.size, dtype=torch.int16, device="cuda")
+    d_res = torch.empty(3, dtype=torch.int64, device="cuda")
+    r = g.utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws, d_res)
+    ref, ref_out = oracle.utf8_to_utf16(d8)
+    assert tuple(r) == tuple(ref)
+    assert np.array_equal(h_out.numpy().view(np.uint16)[:r.written], ref_out)
+
+    d16 = W.utf16_text(10, 100000, W.MIX_CJK_EMOJI)
+    h_in = torch.from_numpy(d16.view(np.int16)).pin_memory()
+    h_out = torch.empty(3 * d16.size, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(d16.size, dtype=torch.int16, device="cuda")
+    d_out = torch.empty(3 * d16.size, dtype=torch.uint8, device="cuda")
+    r = g.utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws, d_res)
+    ref, ref_out = oracle.utf16_to_utf8(d16)
+    assert tuple(r) == tuple(ref)
+    assert np.array_equal(h_out.numpy()[:r.written], ref_out)
+
+
+# ---------------------------------------------------------------------------
+# The benchmark workloads at full size
+# ---------------------------------------------------------------------------
+def test_latin_cyrillic_utf8_1mib(g, ws):
+    d = W.latin_cyrillic_utf8_1mib()
+    r = check_8to16(g, ws, d)
+    assert r.error == oracle.OK and r.position == d.size
+    check_passes8(g, ws, d)
+
+
+def test_cjk_emoji_utf16_256mib(g, ws):
+    d = W.cjk_emoji_utf16_256mib()
+    inp = dev_u16(d)
+    out = torch.empty(3 * d.size, dtype=torch.uint8, device="cuda")
+    res, _ = g.utf16_to_utf8(inp, out=out, ws=ws)
+    ref, ref_out = oracle.utf16_to_utf8(d)
+    assert tuple(res) == tuple(ref) and res.error == oracle.OK
+    assert torch.equal(out[:res.written].cpu(), torch.from_numpy(ref_out))
+    assert tuple(g.validate_utf16(inp, ws=ws)) == tuple(oracle.validate_utf16(d))
+    assert g.utf8_length_from_utf16(inp, ws=ws) == ref.written
+
+
+def test_four_byte_heavy_utf8_64mib_every_error(g, ws):
+    et = W.four_byte_heavy_utf8_64mib()
+    assert len(et.tokens) > 30
+    out = torch.empty(et.data.size, dtype=torch.int16, device="cuda")
+    # (i) the buffer with all its errors: the first one is reported
+    res, _ = g.utf8_to_utf16(dev_u8(et.data), out=out, ws=ws)
+    ref, ref_out = oracle.utf8_to_utf16(et.data)
+    assert tuple(res) == tuple(ref) == (et.tokens[0][2], et.tokens[0][0], ref.written)
+    assert np.array_equal(out[:res.written].cpu().numpy().view(np.uint16), ref_out)
+    # (ii) with errors before k repaired, error k is the first
+    for k, (off, _ln, cls) in enumerate(et.tokens):
+        d = et.repaired_before(k)
+        res, _ = g.utf8_to_utf16(dev_u8(d), out=out, ws=ws)
+        v = g.validate_utf8(dev_u8(d), ws=ws)
+        assert (res.error, res.position) == (cls, off) == (v.error, v.position), k
+        ref = oracle.utf8_to_utf16(d)[0]
+        assert tuple(res) == tuple(ref)
+    # (iii) the clean buffer
+    clean = et.repaired_before(len(et.tokens))
+    res, _ = g.utf8_to_utf16(dev_u8(clean), out=out, ws=ws)
+    ref, ref_out = oracle.utf8_to_utf16(clean)
+    assert tuple(res) == tuple(ref) and res.error == oracle.OK
+    assert np.array_equal(out[:res.written].cpu().numpy().view(np.uint16), ref_out)
+    assert g.utf16_length_from_utf8(dev_u8(clean), ws=ws) == ref.written

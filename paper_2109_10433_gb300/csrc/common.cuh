@@ -168,6 +168,35 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *warp_s
     return warp_sums[warp] + inc - v;
 }
 
+/* As block_exclusive, also OR-ing a flag over the block into *any.
+ * `warp_sums` holds at least THREADS/32 + 2 words. */
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_or(uint32_t v, bool flag, uint32_t *warp_sums,
+                                                       uint32_t *total, bool *any)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_inclusive(v);
+    const unsigned f = __ballot_sync(FULL_MASK, flag);
+    if (lane == 31) warp_sums[warp] = inc | (f ? 0x80000000u : 0u);
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < WARPS ? warp_sums[lane] : 0;
+        const unsigned fl = __ballot_sync(FULL_MASK, (s >> 31) != 0);
+        s &= 0x7FFFFFFFu;
+        uint32_t si = warp_inclusive(s);
+        if (lane < WARPS) warp_sums[lane] = si - s;
+        if (lane == 31) {
+            warp_sums[WARPS] = si;
+            warp_sums[WARPS + 1] = fl ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    *total = warp_sums[WARPS];
+    *any = warp_sums[WARPS + 1] != 0;
+    return warp_sums[warp] + inc - v;
+}
+
 /* Block-wide minimum of 64-bit values into *out (shared); contains syncs. */
 template <int THREADS>
 __device__ __forceinline__ uint64_t block_min(uint64_t v, unsigned long long *scratch)
@@ -242,6 +271,78 @@ __device__ __forceinline__ void st_stream16(void *p, uint4 v)
     asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
                  "r"(v.z), "r"(v.w)
                  : "memory");
+}
+
+/* ---------------------------------------------------------------------------
+ * 1-D TMA bulk copies (global -> shared, completion counted on an mbarrier).
+ * Copies start on 16-byte boundaries and move multiples of 16 bytes.  No
+ * multicast.
+ * ------------------------------------------------------------------------- */
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+/* Orders this thread's earlier shared-memory accesses before later
+ * accesses by the async (TMA) proxy. */
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+/* Upper bound on polls of one mbarrier phase (each poll itself waits a
+ * little in hardware); past it the caller records a timeout. */
+constexpr int MBAR_SPIN_LIMIT = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+{
+    for (int i = 0; i < MBAR_SPIN_LIMIT; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4 &v, int k)

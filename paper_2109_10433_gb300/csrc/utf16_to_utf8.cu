@@ -79,21 +79,6 @@ __device__ __forceinline__ bool has_surrogate(uint32_t x)
     return ((y - 0x00010001u) & ~y & 0x80008000u) != 0;
 }
 
-/* UTF-8 bytes of unit u (byte 0 first, little-endian in the word) and their
- * count; `prev` is the unit before u, used when u is a low surrogate. */
-__device__ __forceinline__ uint32_t encode_unit(uint32_t u, uint32_t prev, int *len)
-{
-    const uint32_t two = (u >> 6) | ((u & 0x3F) << 8) | 0x80C0u;
-    const uint32_t three = (u >> 12) | (((u >> 6) & 0x3F) << 8) | ((u & 0x3F) << 16) | 0x8080E0u;
-    const uint32_t ch = (u & 0x3FF) + 0x40;                  /* code point >> 10, from a high unit */
-    const uint32_t high = (ch >> 8) | (((ch >> 2) & 0x3F) << 8) | 0x80F0u;
-    const uint32_t cp = (prev & 0x3FF) + 0x40;               /* code point >> 10, from the unit before */
-    const uint32_t low = ((cp & 3) << 4) | ((u >> 6) & 0xF) | ((u & 0x3F) << 8) | 0x8080u;
-    const bool sur = (u & 0xF800) == 0xD800;
-    *len = u < 0x80 ? 1 : ((u < 0x800 || sur) ? 2 : 3);
-    return u < 0x80 ? u : (u < 0x800 ? two : (sur ? ((u & 0x400) ? low : high) : three));
-}
-
 /* Append `len` bytes held in `v` to a thread's run of staged bytes.  Full
  * words are stored; the first word (when the run starts inside a word) and
  * the last partial word are shared with the neighbouring threads' runs and
@@ -131,165 +116,274 @@ struct Packer {
     }
 };
 
-template <int THREADS, int WORDS>
+/* Output bytes of a unit by value (1, 2 or 3; 2 for a surrogate unit). */
+__device__ __forceinline__ uint32_t len8(uint32_t u)
+{
+    return u < 0x80 ? 1u : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2u : 3u);
+}
+
+/* The UTF-8 bytes of a BMP unit that is not a surrogate (byte 0 first):
+ * 1 byte below 0x80, 110xxxxx 10xxxxxx below 0x800, else
+ * 1110xxxx 10xxxxxx 10xxxxxx.  For a surrogate the value is a placeholder
+ * of the right length, overwritten by the surrogate pass. */
+__device__ __forceinline__ uint32_t encode_bmp(uint32_t u, uint32_t len)
+{
+    const uint32_t three = (u >> 12) | ((u << 2) & 0x3F00u) | ((u << 16) & 0x3F0000u) | 0x8080E0u;
+    const uint32_t two = (three >> 8) | 0x40u;
+    return len == 1 ? u : (len == 2 ? two : three);
+}
+
+/* The two UTF-8 bytes written for surrogate unit u (p = the unit before it):
+ * a high unit D800-DBFF gives the first two bytes of its character,
+ * 11110xxx 10xxxxxx from c >> 10 = (u & 0x3FF) + 0x40; a low unit gives the
+ * last two, 10xxxxxx 10xxxxxx, from the low two bits of c >> 10 (those of
+ * p) and the ten bits of u (Section 3 pair construction; Fig. 4). */
+__device__ __forceinline__ void surrogate_bytes(uint32_t u, uint32_t p, uint32_t *b0, uint32_t *b1)
+{
+    if (u & 0x400) {
+        *b0 = 0x80u | ((p & 3u) << 4) | ((u >> 6) & 0xFu);
+        *b1 = 0x80u | (u & 0x3Fu);
+    } else {
+        const uint32_t ch = (u & 0x3FFu) + 0x40u;
+        *b0 = 0xF0u | (ch >> 8);
+        *b1 = 0x80u | ((ch >> 2) & 0x3Fu);
+    }
+}
+
+constexpr int HALO16 = 8;   /* units staged on each side of a tile (16 bytes) */
+
+template <int THREADS, int UPT, int STAGES>
+struct U16Layout {
+    static constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    static constexpr int STAGE_UNITS = (int)TILE + 2 * HALO16;
+    static constexpr uint32_t STAGE_BYTES = (uint32_t)STAGE_UNITS * 2;
+    static constexpr uint32_t OUT_WORDS = (uint32_t)((3 * TILE + 16) / 4);
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)OUT_WORDS * 4;
+    static_assert(STAGE_BYTES % 16 == 0 && OUT_WORDS % 4 == 0, "16-byte granules");
+};
+
+/*
+ * Persistent transcoder: each CTA loops over tiles taken from the ticket
+ * counter.  Thread 0 keeps STAGES-1 tiles in flight: their input (plus 8
+ * units of halo on each side) is fetched into a shared-memory ring by 1-D TMA
+ * bulk copies that complete on per-stage mbarriers, and the ticket for the
+ * tile after those is requested one iteration before it is needed.  Tiles
+ * at the ends of the buffer (halo outside the input) are filled by the
+ * threads with guarded loads instead.
+ */
+template <int THREADS, int UPT, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, DevResult *res)
+                     uint64_t status_words, uint64_t tiles, DevResult *res)
 {
-    constexpr int UPT = 2 * WORDS;
-    constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    using Lay = U16Layout<THREADS, UPT, STAGES>;
+    constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
-    constexpr uint32_t STAGE_WORDS = (uint32_t)((3 * TILE + 16) / 4);
-    __shared__ uint32_t s_warp[WARPS + 1];
+    constexpr int WORDS = UPT / 2;
+    static_assert(UPT % 8 == 0 && UPT <= 16, "whole 16-byte vectors, 2-bit lengths in 32 bits");
+    extern __shared__ uint4 smem4[];
+    uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
+    uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
+    uint32_t *outw = reinterpret_cast<uint32_t *>(outw4);
+    uint8_t *outb = reinterpret_cast<uint8_t *>(outw4);
+    __shared__ unsigned long long s_bar[STAGES];
+    __shared__ unsigned long long s_ring[STAGES];
+    __shared__ uint32_t s_warp[WARPS + 2];
     __shared__ unsigned long long s_min[WARPS];
     __shared__ unsigned long long s_tile_excl;
-    __shared__ unsigned s_tile, s_flag;
-    extern __shared__ uint4 s_stage4[];
-    uint32_t *stage = reinterpret_cast<uint32_t *>(s_stage4);
+    __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = (unsigned)atomicAdd(&hdr->ticket, 1ull);
-    for (uint32_t i = tid; i < STAGE_WORDS / 4; i += THREADS) s_stage4[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
-
     const uint64_t head = ((uintptr_t)in & 15) / 2;
     const uint16_t *base = in - head;
     const uint64_t endx = head + n;
-    const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
+    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
 
-    /* 1. load */
-    uint32_t w[WORDS];
-    const bool interior = load_chunk16<WORDS>(base, e0, head, endx, w);
-    uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
-    uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
-    if (lane == 0) pu = unit_at(base, (long long)e0 - 1, head, endx);
-    if (lane == 31) nu = unit_at(base, (long long)(e0 + UPT), head, endx);
-
-    /* which units are input units (edge chunks only) */
-    uint32_t inr = (1u << UPT) - 1;
-    if (!interior) {
-        inr = 0;
-#pragma unroll
-        for (int k = 0; k < UPT; k++) {
-            const long long ex = (long long)(e0 + k);
-            inr |= (ex >= (long long)head && ex < (long long)endx) ? (1u << k) : 0u;
-        }
-    }
-
-    /* 3. lengths; 2. any surrogate / all ASCII */
-    uint32_t total = 0;
-    bool sur = false;
-    uint32_t any = 0;
-#pragma unroll
-    for (int k = 0; k < WORDS; k++) {
-        const uint32_t x = w[k];
-        any |= x;
-        sur |= has_surrogate(x);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t u = (x >> (16 * h)) & 0xFFFF;
-            const uint32_t l = u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
-            total += (inr >> (2 * k + h)) & 1 ? l : 0;
-        }
-    }
-    const bool ascii = (any & 0xFF80FF80u) == 0;
-
-    /* 2. validation where surrogates appear */
-    uint64_t first_err = NONE;
-    if (sur) {
-        uint32_t prev = pu;
-#pragma unroll
-        for (int k = 0; k < UPT; k++) {
-            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
-            const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
-            const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
-            if (bad && ((inr >> k) & 1) && first_err == NONE) first_err = e0 + k - head;
-            prev = u;
-        }
-    }
-
-    /* block scan and look-back */
-    uint32_t tile_total;
-    const uint32_t excl_local = block_exclusive<THREADS>(total, s_warp, &tile_total);
-    if (warp == 0) {
-        uint64_t excl = 0;
-        if (tile == 0) {
-            if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
+    /* thread 0: put tile t in flight into stage s */
+    auto issue = [&](unsigned long long t, int s) {
+        s_ring[s] = t;
+        if (t >= tiles) return;
+        const uint64_t x0 = t * TILE;
+        if (x0 >= head + HALO16 && x0 + TILE + HALO16 <= endx) {
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&s_bar[s], Lay::STAGE_BYTES);
+            bulk_load(stages + (size_t)s * Lay::STAGE_UNITS, base + x0 - HALO16, Lay::STAGE_BYTES, &s_bar[s]);
         } else {
-            if (lane == 0) st_release(status + tile, make_status(epoch, ST_AGGREGATE, tile_total));
-            excl = look_back(status, (long long)tile, epoch, &hdr->flags);
-            if (lane == 0) st_release(status + tile, make_status(epoch, ST_PREFIX, excl + tile_total));
+            mbar_arrive(&s_bar[s]);
         }
-        if (lane == 0) s_tile_excl = excl;
+    };
+
+    unsigned long long pending = 0;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        fence_mbar_init();
+        for (int s = 0; s < STAGES - 1; s++) issue(atomicAdd(&hdr->ticket, 1ull), s);
+        pending = atomicAdd(&hdr->ticket, 1ull);
     }
     __syncthreads();
-    const uint64_t G0 = s_tile_excl;
 
-    /* 4. encode into the staging buffer */
-    const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
-    uint64_t g = G0 + excl_local;
-    uint64_t cap_first = NONE;
-    Packer pk;
-    pk.start(shift + excl_local);
-    if (__all_sync(FULL_MASK, ascii)) {
+    for (int it = 0;; it++) {
+        const int s = it % STAGES;
+        const unsigned long long t = s_ring[s];
+        if (t >= tiles) break;
+        if (tid == 0) {
+            issue(pending, (it + STAGES - 1) % STAGES);
+            pending = atomicAdd(&hdr->ticket, 1ull);
+        }
+        const uint64_t x0 = t * TILE;
+        uint16_t *sb = stages + (size_t)s * Lay::STAGE_UNITS;
+        const bool interior = x0 >= head + HALO16 && x0 + TILE + HALO16 <= endx;
+
+        /* zero the output staging: the previous tile's write-out is done */
+        for (uint32_t i = tid; i < Lay::OUT_WORDS / 4; i += THREADS) outw4[i] = make_uint4(0, 0, 0, 0);
+        if (interior) {
+            if (!mbar_wait(&s_bar[s], (uint32_t)((it / STAGES) & 1))) atomicOr(&hdr->flags, FLAG_TIMEOUT);
+        } else {
+            for (int i = tid; i < Lay::STAGE_UNITS; i += THREADS)
+                sb[i] = (uint16_t)unit_at(base, (long long)(x0 + i) - HALO16, head, endx);
+            __syncthreads();
+        }
+
+        /* this thread's units, the unit before and the unit after */
+        const int i0 = HALO16 + tid * UPT;
+        uint32_t w[WORDS];
+#pragma unroll
+        for (int v = 0; v < WORDS / 4; v++) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
+            w[4 * v + 0] = q.x;
+            w[4 * v + 1] = q.y;
+            w[4 * v + 2] = q.z;
+            w[4 * v + 3] = q.w;
+        }
+        const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
+        const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
+        uint32_t inr = (UPT == 32) ? 0xFFFFFFFFu : ((1u << UPT) - 1);
+        if (!interior) {
+            inr = 0;
+#pragma unroll
+            for (int k = 0; k < UPT; k++)
+                inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
+        }
+#define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
+
+        /* lengths (2 bits per unit) and surrogate positions */
+        uint32_t lens = 0, total = 0, surm = 0;
 #pragma unroll
         for (int k = 0; k < UPT; k++) {
-            if ((inr >> k) & 1) {
-                const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFF;
-                if (g >= cap && cap_first == NONE) cap_first = e0 + k - head;
-                pk.put(stage, u, 1);
-                g++;
+            const uint32_t u = UNIT(k);
+            uint32_t l = len8(u);
+            if (!interior) l = ((inr >> k) & 1) ? l : 0;
+            lens |= l << (2 * k);
+            total += l;
+            surm |= ((u & 0xF800) == 0xD800) ? (1u << k) : 0u;
+        }
+        surm &= inr;
+
+        /* validation where surrogates appear (Section 3) */
+        uint64_t first_err = NONE;
+        if (surm) {
+            uint32_t prev = pu;
+#pragma unroll
+            for (int k = 0; k < UPT; k++) {
+                const uint32_t u = UNIT(k);
+                const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : nu;
+                const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
+                if (bad && ((surm >> k) & 1) && first_err == NONE) first_err = (uint64_t)(e0 + k) - head;
+                prev = u;
             }
         }
-    } else {
-        uint32_t prev = pu;
+
+        /* block scan, then the tile's offset by decoupled look-back */
+        uint32_t tile_total;
+        bool any_err;
+        const uint32_t excl_local =
+            block_exclusive_or<THREADS>(total, first_err != NONE, s_warp, &tile_total, &any_err);
+        if (warp == 0) {
+            uint64_t excl = 0;
+            if (t == 0) {
+                if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
+            } else {
+                if (lane == 0) st_release(status + t, make_status(epoch, ST_AGGREGATE, tile_total));
+                excl = look_back(status, (long long)t, epoch, &hdr->flags);
+                if (lane == 0) st_release(status + t, make_status(epoch, ST_PREFIX, excl + tile_total));
+            }
+            if (lane == 0) s_tile_excl = excl;
+        }
+        __syncthreads();
+        const uint64_t G0 = s_tile_excl;
+        const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
+        const uint32_t my0 = shift + excl_local;   /* staging byte of my first output byte */
+
+        /* encode every unit into packed words of the staging buffer */
+        Packer pk;
+        pk.start(my0);
 #pragma unroll
         for (int k = 0; k < UPT; k++) {
-            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
-            if ((inr >> k) & 1) {
-                int len;
-                const uint32_t v = encode_unit(u, prev, &len);
-                /* a character starts here unless u is the low half of a pair;
-                 * a pair needs its 4 bytes to fit */
-                const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
+            const uint32_t u = UNIT(k);
+            const uint32_t l = (lens >> (2 * k)) & 3;
+            uint32_t v = encode_bmp(u, l);
+            if (!interior) v = l ? v : 0;
+            pk.put(outw, v, (int)l);
+        }
+        pk.finish(outw);
+
+        /* surrogate units: their two bytes, once every packed word is in place */
+        if (__syncthreads_or(surm != 0)) {
+            uint32_t m = surm;
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t below = lens & ((1u << (2 * k)) - 1);
+                const uint32_t o = my0 + __popc(below & 0x55555555u) + 2 * __popc(below & 0xAAAAAAAAu);
+                uint32_t b0, b1;
+                surrogate_bytes(sb[i0 + k], sb[i0 + k - 1], &b0, &b1);
+                outb[o] = (uint8_t)b0;
+                outb[o + 1] = (uint8_t)b1;
+            }
+            __syncthreads();
+        }
+
+        /* write the tile's output bytes [G0, G0 + cnt), clipped to the capacity */
+        const uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
+        uint8_t *gbase = out + G0 - shift;
+        const uint32_t lim = shift + (uint32_t)cnt;
+        const uint32_t nvec = (lim + 15) / 16;
+        for (uint32_t i = tid; i < nvec; i += THREADS) {
+            const uint32_t lo = 16 * i, hi = lo + 16;
+            if (lo >= shift && hi <= lim) {
+                st_stream16(gbase + lo, outw4[i]);
+            } else {
+                for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = outb[b];
+            }
+        }
+
+        /* the first character whose bytes do not fit (only in the tile that
+         * crosses the capacity) */
+        if (G0 <= cap && G0 + tile_total > cap) {
+            uint64_t cap_first = NONE;
+            uint64_t g = G0 + excl_local;
+            uint32_t prev = pu;
+#pragma unroll
+            for (int k = 0; k < UPT; k++) {
+                const uint32_t u = UNIT(k);
+                const uint32_t l = (lens >> (2 * k)) & 3;
+                const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : nu;
                 const bool pair_tail = is_low(u) && is_high(prev);
-                const uint32_t need = (is_high(u) && is_low(next)) ? 4 : len;
-                if (!pair_tail && g + need > cap && cap_first == NONE) cap_first = e0 + k - head;
-                pk.put(stage, v, len);
-                g += len;
+                const uint32_t need = (is_high(u) && is_low(next)) ? 4 : l;
+                if (l && !pair_tail && g + need > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
+                g += l;
+                prev = u;
             }
-            prev = u;
+            const uint64_t m = block_min<THREADS>(cap_first, s_min);
+            if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
         }
-    }
-    pk.finish(stage);
-
-    /* 5. first error and first character that does not fit */
-    if (__syncthreads_or(first_err != NONE)) {
-        const uint64_t m = block_min<THREADS>(first_err, s_min);
-        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
-    }
-    if (G0 <= cap && G0 + tile_total > cap) {
-        const uint64_t m = block_min<THREADS>(cap_first, s_min);
-        if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
-    }
-    __syncthreads();
-
-    /* write the tile's output bytes [G0, G0 + cnt), clipped to the capacity */
-    const uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
-    uint8_t *gbase = out + G0 - shift;
-    const uint8_t *sbytes = reinterpret_cast<const uint8_t *>(stage);
-    const uint32_t lim = shift + (uint32_t)cnt;
-    const uint32_t nvec = (lim + 15) / 16;
-    for (uint32_t i = tid; i < nvec; i += THREADS) {
-        const uint32_t lo = 16 * i, hi = lo + 16;
-        if (lo >= shift && hi <= lim) {
-            st_stream16(gbase + lo, s_stage4[i]);
-        } else {
-            for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = sbytes[b];
+        if (any_err) {
+            const uint64_t m = block_min<THREADS>(first_err, s_min);
+            if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
         }
+#undef UNIT
+        __syncthreads();
     }
 
     /* the CTA that finishes last writes the result */
@@ -311,16 +405,13 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     }
     uint64_t written = 0;
     if (error == GPUTF_E_OK) {
-        written = ld_relaxed(status + gridDim.x - 1) & VALUE_MASK;
+        written = ld_relaxed(status + tiles - 1) & VALUE_MASK;
     } else if (error != GPUTF_E_TIMEOUT) {
         const uint64_t t = (head + pos) / TILE;
         const uint64_t before = t ? (ld_relaxed(status + t - 1) & VALUE_MASK) : 0;
         const uint64_t start = t * TILE > head ? t * TILE - head : 0;
         uint32_t c = 0;
-        for (uint64_t i = start + tid; i < pos; i += THREADS) {
-            const uint32_t u = in[i];
-            c += u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
-        }
+        for (uint64_t i = start + tid; i < pos; i += THREADS) c += len8(in[i]);
         uint32_t sum;
         block_exclusive<THREADS>(c, s_warp, &sum);
         written = before + sum;
@@ -431,24 +522,32 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
  * Launchers.
  * ---------------------------------------------------------------------- */
 constexpr int U16_THREADS = 256;
-constexpr int U16_WORDS = 8;    /* 16 units per thread, 4096-unit tiles */
-constexpr uint64_t U16_TILE = (uint64_t)U16_THREADS * 2 * U16_WORDS;
+constexpr int U16_UPT = 16;     /* 4096-unit tiles */
+constexpr int U16_STAGES = 3;
+using U16Lay = U16Layout<U16_THREADS, U16_UPT, U16_STAGES>;
 
 uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
 {
-    return (((uintptr_t)in % 16) / 2 + n + U16_TILE) / U16_TILE;   /* at least one tile */
+    return (((uintptr_t)in % 16) / 2 + n + U16Lay::TILE) / U16Lay::TILE;   /* at least one tile */
 }
 
 cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
-                                 void *ws, uint64_t status_words, DevResult *res,
+                                 void *ws, uint64_t status_words, DevResult *res, int sms,
                                  cudaStream_t stream)
 {
+    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES>;
+    static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U16_THREADS, U16Lay::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
     const uint64_t tiles = utf16_to_utf8_tiles(in, n);
-    const size_t smem = ((3 * U16_TILE + 16) / 4) * 4;
+    const uint64_t grid = tiles < (uint64_t)sms * per_sm ? tiles : (uint64_t)sms * per_sm;
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
-    utf16_to_utf8_kernel<U16_THREADS, U16_WORDS><<<(unsigned)tiles, U16_THREADS, smem, stream>>>(
-        in, n, out, cap, hdr, status, status_words, res);
+    kern<<<(unsigned)grid, U16_THREADS, U16Lay::SMEM, stream>>>(in, n, out, cap, hdr, status,
+                                                                 status_words, tiles, res);
     return cudaGetLastError();
 }
 

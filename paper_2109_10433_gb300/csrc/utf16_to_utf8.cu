@@ -116,6 +116,34 @@ struct Packer {
     }
 };
 
+/* Branch-free packing for interior tiles, where every thread writes at least
+ * UPT >= 4 bytes and so fills at least one whole word.  Full words are
+ * stored; a thread's first word is stored with only its own bytes, and its
+ * last partial word is handed to the next thread (through shared memory),
+ * which ORs it into that shared word after a barrier. */
+struct WordPacker {
+    uint32_t cur;     /* bytes gathered for word `widx` */
+    uint32_t nbits;   /* bits of `cur` filled, 0..31 */
+    uint32_t widx;
+    __device__ __forceinline__ void start(uint32_t byte_pos)
+    {
+        cur = 0;
+        nbits = 8 * (byte_pos & 3);
+        widx = byte_pos >> 2;
+    }
+    __device__ __forceinline__ void put(uint32_t *stage, uint32_t v, uint32_t len)
+    {
+        const uint32_t lo = cur | (v << nbits);
+        const uint32_t hi = __funnelshift_l(v, 0u, nbits);   /* bits of v past the word; 0 when nbits = 0 */
+        nbits += 8 * len;
+        const bool full = nbits >= 32;
+        if (full) stage[widx] = lo;
+        widx += full ? 1u : 0u;
+        cur = full ? hi : lo;
+        nbits -= full ? 32u : 0u;
+    }
+};
+
 /* Output bytes of a unit by value (1, 2 or 3; 2 for a surrogate unit). */
 __device__ __forceinline__ uint32_t len8(uint32_t u)
 {
@@ -163,13 +191,23 @@ struct U16Layout {
 };
 
 /*
- * Persistent transcoder: each CTA loops over tiles taken from the ticket
- * counter.  Thread 0 keeps STAGES-1 tiles in flight: their input (plus 8
- * units of halo on each side) is fetched into a shared-memory ring by 1-D TMA
- * bulk copies that complete on per-stage mbarriers, and the ticket for the
- * tile after those is requested one iteration before it is needed.  Tiles
- * at the ends of the buffer (halo outside the input) are filled by the
- * threads with guarded loads instead.
+ * Persistent transcoder, software-pipelined over tiles.  Each iteration of a
+ * CTA's loop does, for the tile n whose input just arrived and the tile c
+ * before it:
+ *   phase A(n): per-unit lengths, validation, block scan; publish n's
+ *               aggregate (and its first error);
+ *   look-back(c): c's exclusive output offset; publish c's inclusive prefix;
+ *   phase B(c): encode c's units into the staging buffer, write them out;
+ *   then take a new ticket and start its input copy into the freed stage.
+ * So every look-back runs one iteration after its own aggregate went out,
+ * when the tiles before it have long published theirs, and a CTA only waits
+ * (in a look-back) while every ticket it holds has its aggregate published:
+ * no tile ever waits behind work queued in another CTA.
+ *
+ * Input tiles (plus 8 units of halo on each side) arrive in a three-stage
+ * shared-memory ring by 1-D TMA bulk copies completing on per-stage
+ * mbarriers.  Tiles at the ends of the buffer (halo outside the input) are
+ * filled by the threads with guarded loads instead.
  */
 template <int THREADS, int UPT, int STAGES>
 __global__ void __launch_bounds__(THREADS)
@@ -182,6 +220,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     constexpr int WARPS = THREADS / 32;
     constexpr int WORDS = UPT / 2;
     static_assert(UPT % 8 == 0 && UPT <= 16, "whole 16-byte vectors, 2-bit lengths in 32 bits");
+    static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
     extern __shared__ uint4 smem4[];
     uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
     uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
@@ -191,10 +230,12 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     __shared__ unsigned long long s_ring[STAGES];
     __shared__ uint32_t s_warp[WARPS + 2];
     __shared__ unsigned long long s_min[WARPS];
-    __shared__ unsigned long long s_tile_excl;
+    __shared__ unsigned long long s_lb_sum[WARPS];
+    __shared__ unsigned s_lb_has[WARPS];
+    __shared__ uint32_t s_hand[THREADS];
     __shared__ unsigned s_flag;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const uint64_t head = ((uintptr_t)in & 15) / 2;
     const uint16_t *base = in - head;
     const uint64_t endx = head + n;
@@ -214,177 +255,254 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         }
     };
 
-    unsigned long long pending = 0;
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
-        for (int s = 0; s < STAGES - 1; s++) issue(atomicAdd(&hdr->ticket, 1ull), s);
-        pending = atomicAdd(&hdr->ticket, 1ull);
+        issue(atomicAdd(&hdr->ticket, 1ull), 0);
+        issue(atomicAdd(&hdr->ticket, 1ull), 1);
     }
     __syncthreads();
 
-    for (int it = 0;; it++) {
-        const int s = it % STAGES;
-        const unsigned long long t = s_ring[s];
-        if (t >= tiles) break;
-        if (tid == 0) {
-            issue(pending, (it + STAGES - 1) % STAGES);
-            pending = atomicAdd(&hdr->ticket, 1ull);
-        }
-        const uint64_t x0 = t * TILE;
-        uint16_t *sb = stages + (size_t)s * Lay::STAGE_UNITS;
-        const bool interior = x0 >= head + HALO16 && x0 + TILE + HALO16 <= endx;
+    /* state of tile c (phase A done, phase B pending) */
+    bool have_c = false, c_interior = false;
+    unsigned long long c_tile = 0;
+    uint32_t c_total = 0, c_excl = 0, c_lens = 0, c_surm = 0;
+    int c_stage = 0;
 
-        /* zero the output staging: the previous tile's write-out is done */
-        for (uint32_t i = tid; i < Lay::OUT_WORDS / 4; i += THREADS) outw4[i] = make_uint4(0, 0, 0, 0);
-        if (interior) {
-            if (!mbar_wait(&s_bar[s], (uint32_t)((it / STAGES) & 1))) atomicOr(&hdr->flags, FLAG_TIMEOUT);
-        } else {
-            for (int i = tid; i < Lay::STAGE_UNITS; i += THREADS)
-                sb[i] = (uint16_t)unit_at(base, (long long)(x0 + i) - HALO16, head, endx);
-            __syncthreads();
-        }
-
-        /* this thread's units, the unit before and the unit after */
-        const int i0 = HALO16 + tid * UPT;
-        uint32_t w[WORDS];
-#pragma unroll
-        for (int v = 0; v < WORDS / 4; v++) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
-            w[4 * v + 0] = q.x;
-            w[4 * v + 1] = q.y;
-            w[4 * v + 2] = q.z;
-            w[4 * v + 3] = q.w;
-        }
-        const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
-        const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
-        uint32_t inr = (UPT == 32) ? 0xFFFFFFFFu : ((1u << UPT) - 1);
-        if (!interior) {
-            inr = 0;
-#pragma unroll
-            for (int k = 0; k < UPT; k++)
-                inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
-        }
 #define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
-
-        /* lengths (2 bits per unit) and surrogate positions */
-        uint32_t lens = 0, total = 0, surm = 0;
+    for (int it = 0;; it++) {
+        /* ---------------- phase A of tile n ---------------- */
+        const int sn = it % STAGES;
+        const unsigned long long t = s_ring[sn];
+        const bool have_n = t < tiles;
+        uint32_t n_total = 0, n_excl = 0, n_lens = 0, n_surm = 0;
+        const bool interior = have_n && t * TILE >= head + HALO16 && t * TILE + TILE + HALO16 <= endx;
+        if (have_n) {
+            const uint64_t x0 = t * TILE;
+            uint16_t *sb = stages + (size_t)sn * Lay::STAGE_UNITS;
+            if (interior) {
+                if (!mbar_wait(&s_bar[sn], (uint32_t)((it / STAGES) & 1))) atomicOr(&hdr->flags, FLAG_TIMEOUT);
+            } else {
+                for (int i = tid; i < Lay::STAGE_UNITS; i += THREADS)
+                    sb[i] = (uint16_t)unit_at(base, (long long)(x0 + i) - HALO16, head, endx);
+                __syncthreads();
+            }
+            const int i0 = HALO16 + tid * UPT;
+            uint32_t w[WORDS];
 #pragma unroll
-        for (int k = 0; k < UPT; k++) {
-            const uint32_t u = UNIT(k);
-            uint32_t l = len8(u);
-            if (!interior) l = ((inr >> k) & 1) ? l : 0;
-            lens |= l << (2 * k);
-            total += l;
-            surm |= ((u & 0xF800) == 0xD800) ? (1u << k) : 0u;
-        }
-        surm &= inr;
-
-        /* validation where surrogates appear (Section 3) */
-        uint64_t first_err = NONE;
-        if (surm) {
-            uint32_t prev = pu;
+            for (int v = 0; v < WORDS / 4; v++) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
+                w[4 * v + 0] = q.x;
+                w[4 * v + 1] = q.y;
+                w[4 * v + 2] = q.z;
+                w[4 * v + 3] = q.w;
+            }
+            const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
+            const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
+            uint32_t inr = (1u << UPT) - 1;
+            if (!interior) {
+                inr = 0;
+#pragma unroll
+                for (int k = 0; k < UPT; k++)
+                    inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
+            }
+            /* lengths (2 bits per unit); high and low surrogate positions */
+            uint32_t himask = 0, lomask = 0;
 #pragma unroll
             for (int k = 0; k < UPT; k++) {
                 const uint32_t u = UNIT(k);
-                const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : nu;
-                const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
-                if (bad && ((surm >> k) & 1) && first_err == NONE) first_err = (uint64_t)(e0 + k) - head;
-                prev = u;
+                uint32_t l = len8(u);
+                if (!interior) l = ((inr >> k) & 1) ? l : 0;
+                n_lens |= l << (2 * k);
+                n_total += l;
+                himask |= is_high(u) ? (1u << k) : 0u;
+                lomask |= is_low(u) ? (1u << k) : 0u;
+            }
+            n_surm = (himask | lomask) & inr;
+            /* Section 3: a high unit must be followed by a low one, a low
+             * unit must follow a high one (neighbours from the halo) */
+            uint64_t first_err = NONE;
+            if (n_surm) {
+                const uint32_t lo_next = (lomask >> 1) | (is_low(nu) ? (1u << (UPT - 1)) : 0u);   /* bit k: unit k+1 is low */
+                const uint32_t prev_hi = (himask << 1) | (is_high(pu) ? 1u : 0u);    /* bit k: unit k-1 is high */
+                const uint32_t errs = ((himask & ~lo_next) | (lomask & ~prev_hi)) & inr;
+                if (errs) first_err = (uint64_t)(e0 + __ffs(errs) - 1) - head;
+            }
+            bool any_err;
+            n_excl = block_exclusive_or<THREADS>(n_total, first_err != NONE, s_warp, &n_total, &any_err);
+            if (tid == 0)
+                st_release(status + t, make_status(epoch, t == 0 ? ST_PREFIX : ST_AGGREGATE, n_total));
+            if (any_err) {
+                const uint64_t m = block_min<THREADS>(first_err, s_min);
+                if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
             }
         }
 
-        /* block scan, then the tile's offset by decoupled look-back */
-        uint32_t tile_total;
-        bool any_err;
-        const uint32_t excl_local =
-            block_exclusive_or<THREADS>(total, first_err != NONE, s_warp, &tile_total, &any_err);
-        if (warp == 0) {
-            uint64_t excl = 0;
-            if (t == 0) {
-                if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
-            } else {
-                if (lane == 0) st_release(status + t, make_status(epoch, ST_AGGREGATE, tile_total));
-                excl = look_back(status, (long long)t, epoch, &hdr->flags);
-                if (lane == 0) st_release(status + t, make_status(epoch, ST_PREFIX, excl + tile_total));
-            }
-            if (lane == 0) s_tile_excl = excl;
-        }
-        __syncthreads();
-        const uint64_t G0 = s_tile_excl;
-        const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
-        const uint32_t my0 = shift + excl_local;   /* staging byte of my first output byte */
+        /* ---------------- look-back and phase B of tile c ---------------- */
+        if (have_c) {
+            const uint16_t *sb = stages + (size_t)c_stage * Lay::STAGE_UNITS;
+            const int i0 = HALO16 + tid * UPT;
+            /* the look-back window's status words are requested now and
+             * examined after packing, so the round trip hides behind it */
+            const long long lb_idx = (long long)c_tile - 1 - tid;
+            const uint64_t lb_word = (c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
 
-        /* encode every unit into packed words of the staging buffer */
-        Packer pk;
-        pk.start(my0);
+            uint32_t w[WORDS];
 #pragma unroll
-        for (int k = 0; k < UPT; k++) {
-            const uint32_t u = UNIT(k);
-            const uint32_t l = (lens >> (2 * k)) & 3;
-            uint32_t v = encode_bmp(u, l);
-            if (!interior) v = l ? v : 0;
-            pk.put(outw, v, (int)l);
-        }
-        pk.finish(outw);
+            for (int v = 0; v < WORDS / 4; v++) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
+                w[4 * v + 0] = q.x;
+                w[4 * v + 1] = q.y;
+                w[4 * v + 2] = q.z;
+                w[4 * v + 3] = q.w;
+            }
+            /* encode every unit into packed words of the staging buffer, at
+             * offsets from the tile's first output byte */
+            if (c_interior) {
+                WordPacker wp;
+                wp.start(c_excl);
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    const uint32_t l = (c_lens >> (2 * k)) & 3;
+                    wp.put(outw, encode_bmp(u, l), l);
+                }
+                s_hand[tid] = wp.nbits ? wp.cur : 0u;
+                __syncthreads();
+                if (tid > 0 && (c_excl & 3)) outw[c_excl >> 2] |= s_hand[tid - 1];
+                if (tid == THREADS - 1 && wp.nbits) outw[wp.widx] = wp.cur;
+            } else {
+                for (uint32_t i = tid; i < Lay::OUT_WORDS / 4; i += THREADS) outw4[i] = make_uint4(0, 0, 0, 0);
+                __syncthreads();
+                Packer pk;
+                pk.start(c_excl);
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    const uint32_t l = (c_lens >> (2 * k)) & 3;
+                    pk.put(outw, l ? encode_bmp(u, l) : 0u, (int)l);
+                }
+                pk.finish(outw);
+            }
 
-        /* surrogate units: their two bytes, once every packed word is in place */
-        if (__syncthreads_or(surm != 0)) {
-            uint32_t m = surm;
-            while (m) {
-                const int k = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t below = lens & ((1u << (2 * k)) - 1);
-                const uint32_t o = my0 + __popc(below & 0x55555555u) + 2 * __popc(below & 0xAAAAAAAAu);
-                uint32_t b0, b1;
-                surrogate_bytes(sb[i0 + k], sb[i0 + k - 1], &b0, &b1);
-                outb[o] = (uint8_t)b0;
-                outb[o + 1] = (uint8_t)b1;
+            /* the window: usable when an inclusive prefix appears in it and
+             * every entry before that one has been published */
+            uint64_t G0 = 0;
+            if (c_tile > 0) {
+                const bool in_window = lb_idx >= 0;
+                const uint64_t flag = in_window ? ((lb_word >> 40) & 3) : ST_PREFIX;
+                const bool ok = !in_window || ((unsigned)(lb_word >> 42) == epoch && flag != 0);
+                const unsigned pmask = __ballot_sync(FULL_MASK, ok && flag == ST_PREFIX);
+                const unsigned bad = __ballot_sync(FULL_MASK, !ok);
+                const int lane = tid & 31, wid = tid >> 5;
+                const int stop = pmask ? __ffs(pmask) - 1 : 31;
+                uint64_t v = (lane <= stop && in_window) ? (lb_word & VALUE_MASK) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+                if (lane == 0) {
+                    s_lb_sum[wid] = v;
+                    s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
+                }
+                __syncthreads();
+                bool found = false, usable = true;
+#pragma unroll
+                for (int k = 0; k < WARPS; k++) {
+                    if (!found && usable) {
+                        usable = (s_lb_has[k] & 2u) == 0;
+                        G0 += s_lb_sum[k];
+                        found = (s_lb_has[k] & 1u) != 0;
+                    }
+                }
+                __syncthreads();
+                if (!(found && usable))   /* rare: fall back to polling */
+                    G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
+                if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
+            } else {
+                __syncthreads();
+            }
+
+            /* surrogate units: their two bytes, once every packed word is in place */
+            if (__syncthreads_or(c_surm != 0)) {
+                uint32_t m = c_surm;
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint32_t below = c_lens & ((1u << (2 * k)) - 1);
+                    const uint32_t o = c_excl + __popc(below & 0x55555555u) + 2 * __popc(below & 0xAAAAAAAAu);
+                    uint32_t b0, b1;
+                    surrogate_bytes(sb[i0 + k], sb[i0 + k - 1], &b0, &b1);
+                    outb[o] = (uint8_t)b0;
+                    outb[o + 1] = (uint8_t)b1;
+                }
+                __syncthreads();
+            }
+
+            /* write the tile's output bytes [G0, G0 + cnt), clipped to the
+             * capacity: aligned 16-byte stores, each assembled from the
+             * staging words by funnel shifts when the destination is not
+             * aligned like the staging buffer */
+            const uint64_t cnt = G0 >= cap ? 0 : (G0 + c_total > cap ? cap - G0 : c_total);
+            const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
+            uint8_t *gbase = out + G0 - shift;      /* 16-byte aligned; byte j <-> staging byte j - shift */
+            const uint32_t lim = shift + (uint32_t)cnt;
+            const uint32_t nvec = (lim + 15) / 16;
+            const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
+            for (uint32_t i = tid; i < nvec; i += THREADS) {
+                const uint32_t lo = 16 * i, hi = lo + 16;
+                if (lo >= shift && hi <= lim) {
+                    const uint32_t j = 4 * i - q;   /* staging word holding the first byte's word-aligned part */
+                    uint4 o;
+                    if (r8 == 0) {
+                        o = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
+                    } else {
+                        const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
+                        o = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
+                                       __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
+                    }
+                    st_stream16(gbase + lo, o);
+                } else {
+                    for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = outb[b - shift];
+                }
+            }
+
+            /* the first character whose bytes do not fit (only in the tile
+             * that crosses the capacity) */
+            if (G0 <= cap && G0 + c_total > cap) {
+                const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * UPT);
+                uint64_t cap_first = NONE;
+                uint64_t g = G0 + c_excl;
+                uint32_t prev = sb[i0 - 1];
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    const uint32_t l = (c_lens >> (2 * k)) & 3;
+                    const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : sb[i0 + UPT];
+                    const bool pair_tail = is_low(u) && is_high(prev);
+                    const uint32_t need = (is_high(u) && is_low(next)) ? 4 : l;
+                    if (l && !pair_tail && g + need > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
+                    g += l;
+                    prev = u;
+                }
+                const uint64_t m = block_min<THREADS>(cap_first, s_min);
+                if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
             }
             __syncthreads();
         }
 
-        /* write the tile's output bytes [G0, G0 + cnt), clipped to the capacity */
-        const uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
-        uint8_t *gbase = out + G0 - shift;
-        const uint32_t lim = shift + (uint32_t)cnt;
-        const uint32_t nvec = (lim + 15) / 16;
-        for (uint32_t i = tid; i < nvec; i += THREADS) {
-            const uint32_t lo = 16 * i, hi = lo + 16;
-            if (lo >= shift && hi <= lim) {
-                st_stream16(gbase + lo, outw4[i]);
-            } else {
-                for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = outb[b];
-            }
-        }
-
-        /* the first character whose bytes do not fit (only in the tile that
-         * crosses the capacity) */
-        if (G0 <= cap && G0 + tile_total > cap) {
-            uint64_t cap_first = NONE;
-            uint64_t g = G0 + excl_local;
-            uint32_t prev = pu;
-#pragma unroll
-            for (int k = 0; k < UPT; k++) {
-                const uint32_t u = UNIT(k);
-                const uint32_t l = (lens >> (2 * k)) & 3;
-                const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : nu;
-                const bool pair_tail = is_low(u) && is_high(prev);
-                const uint32_t need = (is_high(u) && is_low(next)) ? 4 : l;
-                if (l && !pair_tail && g + need > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
-                g += l;
-                prev = u;
-            }
-            const uint64_t m = block_min<THREADS>(cap_first, s_min);
-            if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
-        }
-        if (any_err) {
-            const uint64_t m = block_min<THREADS>(first_err, s_min);
-            if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
-        }
-#undef UNIT
+        /* tile n becomes c; a new tile goes in flight into c's old stage */
+        if (!have_n) break;
+        if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
+        have_c = true;
+        c_interior = interior;
+        c_tile = t;
+        c_total = n_total;
+        c_excl = n_excl;
+        c_lens = n_lens;
+        c_surm = n_surm;
+        c_stage = sn;
         __syncthreads();
     }
+#undef UNIT
 
     /* the CTA that finishes last writes the result */
     if (!finish_cta(hdr, &s_flag)) return;

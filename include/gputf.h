@@ -155,6 +155,32 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream);
 
+/* Largest input, in 16-bit units, that gputf_utf16_to_utf8_static accepts
+ * (32 Mi units, 64 MiB of UTF-16). */
+#define GPUTF_STATIC_MAX_UNITS (((uint64_t)1) << 25)
+
+/* gputf_utf16_to_utf8 for callers that cannot allocate device memory (the
+ * paper has no counterpart: this is a deployment concern).  Some callers
+ * must not call cudaMalloc when they run: code on a stream that is being
+ * captured into a CUDA graph in a mode that forbids it, code inside a custom
+ * allocator or memory-pool callback, where allocating would re-enter the
+ * allocator, or a service that reserves all its memory at start-up.  This
+ * entry point takes no workspace: its scratch is a fixed array inside the
+ * library (about 256 KiB), which every GPU that loads the library keeps until
+ * the process exits.  Arguments, results and units are as for
+ * gputf_utf16_to_utf8.
+ *   - Inputs longer than GPUTF_STATIC_MAX_UNITS are refused with
+ *     GPUTF_STATUS_INPUT_TOO_LARGE; use gputf_utf16_to_utf8 for those.
+ *   - The first call on each device sets the scratch up (it looks up the
+ *     array's device address and enqueues its initialisation on `stream`);
+ *     make that first call before any stream capture.
+ *   - All calls on a device share the one array: calls that overlap on the
+ *     GPU (on different streams without ordering) race and must be avoided.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *     routine. */
+gputf_status gputf_utf16_to_utf8_static(const uint16_t *in, size_t n_units, uint8_t *out,
+                                        size_t out_cap, gputf_result *res, cudaStream_t stream);
+
 /* Names of codes, for messages. */
 const char *gputf_error_name(int32_t error);
 const char *gputf_status_name(gputf_status status);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "gputf_utf8_length_from_utf16": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf8_to_utf16_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
+    "gputf_utf16_to_utf8_static": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_error_name": ([ctypes.c_int32], ctypes.c_char_p),
     "gputf_status_name": ([_I], ctypes.c_char_p),
     "gputf_last_cuda_error": ([], _I),

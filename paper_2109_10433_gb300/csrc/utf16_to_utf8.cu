@@ -83,99 +83,49 @@ __device__ __forceinline__ bool has_surrogate(uint32_t x)
  * words are stored; the first word (when the run starts inside a word) and
  * the last partial word are shared with the neighbouring threads' runs and
  * are OR-ed into the zeroed staging buffer. */
-struct Packer {
-    unsigned long long acc;
-    uint32_t nbits;
-    uint32_t widx;
-    bool first_shared;
-    __device__ __forceinline__ void start(uint32_t byte_pos)
-    {
-        acc = 0;
-        nbits = 8 * (byte_pos & 3);
-        widx = byte_pos >> 2;
-        first_shared = (byte_pos & 3) != 0;
-    }
-    __device__ __forceinline__ void put(uint32_t *stage, uint32_t v, int len)
-    {
-        acc |= (unsigned long long)v << nbits;
-        nbits += 8 * len;
-        if (nbits >= 32) {
-            if (first_shared)
-                atomicOr(stage + widx, (uint32_t)acc);
-            else
-                stage[widx] = (uint32_t)acc;
-            first_shared = false;
-            widx++;
-            acc >>= 32;
-            nbits -= 32;
-        }
-    }
-    __device__ __forceinline__ void finish(uint32_t *stage)
-    {
-        if (nbits) atomicOr(stage + widx, (uint32_t)acc);
-    }
-};
 
-/* Branch-free packing for interior tiles, where every thread writes at least
- * UPT >= 4 bytes and so fills at least one whole word.  Full words are
- * stored; a thread's first word is stored with only its own bytes, and its
- * last partial word is handed to the next thread (through shared memory),
- * which ORs it into that shared word after a barrier. */
-struct WordPacker {
-    uint32_t cur;     /* bytes gathered for word `widx` */
-    uint32_t nbits;   /* bits of `cur` filled, 0..31 */
-    uint32_t widx;
-    __device__ __forceinline__ void start(uint32_t byte_pos)
-    {
-        cur = 0;
-        nbits = 8 * (byte_pos & 3);
-        widx = byte_pos >> 2;
-    }
-    __device__ __forceinline__ void put(uint32_t *stage, uint32_t v, uint32_t len)
-    {
-        const uint32_t lo = cur | (v << nbits);
-        const uint32_t hi = __funnelshift_l(v, 0u, nbits);   /* bits of v past the word; 0 when nbits = 0 */
-        nbits += 8 * len;
-        const bool full = nbits >= 32;
-        if (full) stage[widx] = lo;
-        widx += full ? 1u : 0u;
-        cur = full ? hi : lo;
-        nbits -= full ? 32u : 0u;
-    }
-};
-
-/* Output bytes of a unit by value (1, 2 or 3; 2 for a surrogate unit). */
+/* Output bytes of a unit by value: 1, 2 or 3, and 2 for a surrogate unit
+ * (the closed form of the length pass; Table 2). */
 __device__ __forceinline__ uint32_t len8(uint32_t u)
 {
     return u < 0x80 ? 1u : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2u : 3u);
 }
 
-/* The UTF-8 bytes of a BMP unit that is not a surrogate (byte 0 first):
- * 1 byte below 0x80, 110xxxxx 10xxxxxx below 0x800, else
- * 1110xxxx 10xxxxxx 10xxxxxx.  For a surrogate the value is a placeholder
- * of the right length, overwritten by the surrogate pass. */
-__device__ __forceinline__ uint32_t encode_bmp(uint32_t u, uint32_t len)
+/* Spreads the 8 low bits of x to bit 0 of the eight 4-bit fields of a word. */
+__device__ __forceinline__ uint32_t spread4(uint32_t x)
 {
-    const uint32_t three = (u >> 12) | ((u << 2) & 0x3F00u) | ((u << 16) & 0x3F0000u) | 0x8080E0u;
-    const uint32_t two = (three >> 8) | 0x40u;
-    return len == 1 ? u : (len == 2 ? two : three);
+    x &= 0xFF;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x;
 }
 
-/* The two UTF-8 bytes written for surrogate unit u (p = the unit before it):
- * a high unit D800-DBFF gives the first two bytes of its character,
- * 11110xxx 10xxxxxx from c >> 10 = (u & 0x3FF) + 0x40; a low unit gives the
- * last two, 10xxxxxx 10xxxxxx, from the low two bits of c >> 10 (those of
- * p) and the ten bits of u (Section 3 pair construction; Fig. 4). */
-__device__ __forceinline__ void surrogate_bytes(uint32_t u, uint32_t p, uint32_t *b0, uint32_t *b1)
+/*
+ * Bytes written per unit inside a tile.  A surrogate pair is written whole by
+ * its high unit (4 bytes) and its low unit writes none; every other unit
+ * writes its len8().  Over any run of valid text this adds up to the same
+ * total as len8(), and it lets every unit write its bytes from its own value
+ * and the value of the unit after it:
+ *   1 byte  : u
+ *   2 bytes : 110xxxxx 10xxxxxx                 (u < 0x800)
+ *   3 bytes : 1110xxxx 10xxxxxx 10xxxxxx        (other BMP units)
+ *   4 bytes : 11110xxx 10xxxxxx 10xxxxxx 10xxxxxx of the code point
+ *             c = ((hi - 0xD800) << 10) + (lo - 0xDC00) + 0x10000
+ * (Section 3 pair construction; Section 5 byte layout with lead prefixes
+ * 110 / 1110 / 11110 and continuation prefix 10.)  A lone surrogate (an
+ * error) writes 2 bytes of no meaning; they lie past the valid prefix.
+ */
+__device__ __forceinline__ void put_utf8(uint8_t *dst, uint32_t o, uint32_t u, uint32_t next, uint32_t l)
 {
-    if (u & 0x400) {
-        *b0 = 0x80u | ((p & 3u) << 4) | ((u >> 6) & 0xFu);
-        *b1 = 0x80u | (u & 0x3Fu);
-    } else {
-        const uint32_t ch = (u & 0x3FFu) + 0x40u;
-        *b0 = 0xF0u | (ch >> 8);
-        *b1 = 0x80u | ((ch >> 2) & 0x3Fu);
-    }
+    const uint32_t c = (u << 10) + next - 0x35FDC00u;
+    const uint32_t y = l == 4 ? c : u;
+    const uint32_t end = o + l;
+    const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __funnelshift_r(0xF0E0C000u, 0u, 8 * l - 8);
+    if (l >= 1) dst[o] = (uint8_t)lead;
+    if (l >= 2) dst[end - 1] = (uint8_t)((y & 0x3F) | 0x80);
+    if (l >= 3) dst[end - 2] = (uint8_t)(((y >> 6) & 0x3F) | 0x80);
+    if (l == 4) dst[end - 3] = (uint8_t)(((y >> 12) & 0x3F) | 0x80);
 }
 
 constexpr int HALO16 = 8;   /* units staged on each side of a tile (16 bytes) */
@@ -185,7 +135,7 @@ struct U16Layout {
     static constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
     static constexpr int STAGE_UNITS = (int)TILE + 2 * HALO16;
     static constexpr uint32_t STAGE_BYTES = (uint32_t)STAGE_UNITS * 2;
-    static constexpr uint32_t OUT_WORDS = (uint32_t)((3 * TILE + 16) / 4);
+    static constexpr uint32_t OUT_WORDS = (uint32_t)((3 * TILE + 32) / 4);   /* staging, plus slack */
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)OUT_WORDS * 4;
     static_assert(STAGE_BYTES % 16 == 0 && OUT_WORDS % 4 == 0, "16-byte granules");
 };
@@ -194,15 +144,18 @@ struct U16Layout {
  * Persistent transcoder, software-pipelined over tiles.  Each iteration of a
  * CTA's loop does, for the tile n whose input just arrived and the tile c
  * before it:
- *   phase A(n): per-unit lengths, validation, block scan; publish n's
- *               aggregate (and its first error);
- *   look-back(c): c's exclusive output offset; publish c's inclusive prefix;
- *   phase B(c): encode c's units into the staging buffer, write them out;
+ *   phase A(n): bytes per unit, validation, block scan; publish n's aggregate
+ *               (and its first error);
+ *   phase B(c): c's exclusive output offset by decoupled look-back (its
+ *               status words are requested first and examined after the
+ *               bytes are written); c's bytes into the staging buffer at
+ *               tile-local offsets; publish c's inclusive prefix; write the
+ *               tile out with aligned 16-byte stores;
  *   then take a new ticket and start its input copy into the freed stage.
- * So every look-back runs one iteration after its own aggregate went out,
- * when the tiles before it have long published theirs, and a CTA only waits
- * (in a look-back) while every ticket it holds has its aggregate published:
- * no tile ever waits behind work queued in another CTA.
+ * Every look-back thus runs one iteration after its tile's aggregate went
+ * out, when the tiles before it have long published theirs, and a CTA only
+ * waits (in a look-back) while every ticket it holds has its aggregate
+ * published: no tile ever waits behind work queued in another CTA.
  *
  * Input tiles (plus 8 units of halo on each side) arrive in a three-stage
  * shared-memory ring by 1-D TMA bulk copies completing on per-stage
@@ -219,7 +172,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
     constexpr int WORDS = UPT / 2;
-    static_assert(UPT % 8 == 0 && UPT <= 16, "whole 16-byte vectors, 2-bit lengths in 32 bits");
+    static_assert(UPT == 16, "16 units per thread: two words of 4-bit byte counts");
     static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
     extern __shared__ uint4 smem4[];
     uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
@@ -232,7 +185,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     __shared__ unsigned long long s_min[WARPS];
     __shared__ unsigned long long s_lb_sum[WARPS];
     __shared__ unsigned s_lb_has[WARPS];
-    __shared__ uint32_t s_hand[THREADS];
     __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x;
@@ -264,9 +216,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     __syncthreads();
 
     /* state of tile c (phase A done, phase B pending) */
-    bool have_c = false, c_interior = false;
+    bool have_c = false;
     unsigned long long c_tile = 0;
-    uint32_t c_total = 0, c_excl = 0, c_lens = 0, c_surm = 0;
+    uint32_t c_total = 0, c_excl = 0, c_la = 0, c_lb = 0;
     int c_stage = 0;
 
 #define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
@@ -275,11 +227,11 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         const int sn = it % STAGES;
         const unsigned long long t = s_ring[sn];
         const bool have_n = t < tiles;
-        uint32_t n_total = 0, n_excl = 0, n_lens = 0, n_surm = 0;
-        const bool interior = have_n && t * TILE >= head + HALO16 && t * TILE + TILE + HALO16 <= endx;
+        uint32_t n_total = 0, n_excl = 0, n_la = 0, n_lb = 0;
         if (have_n) {
             const uint64_t x0 = t * TILE;
             uint16_t *sb = stages + (size_t)sn * Lay::STAGE_UNITS;
+            const bool interior = x0 >= head + HALO16 && x0 + TILE + HALO16 <= endx;
             if (interior) {
                 if (!mbar_wait(&s_bar[sn], (uint32_t)((it / STAGES) & 1))) atomicOr(&hdr->flags, FLAG_TIMEOUT);
             } else {
@@ -299,34 +251,41 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             }
             const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
-            uint32_t inr = (1u << UPT) - 1;
+            uint32_t inr = 0xFFFFu;
             if (!interior) {
                 inr = 0;
 #pragma unroll
                 for (int k = 0; k < UPT; k++)
                     inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
             }
-            /* lengths (2 bits per unit); high and low surrogate positions */
+            /* bytes per unit (4-bit fields) and surrogate positions */
             uint32_t himask = 0, lomask = 0;
 #pragma unroll
             for (int k = 0; k < UPT; k++) {
                 const uint32_t u = UNIT(k);
                 uint32_t l = len8(u);
                 if (!interior) l = ((inr >> k) & 1) ? l : 0;
-                n_lens |= l << (2 * k);
+                if (k < 8) n_la |= l << (4 * k);
+                else n_lb |= l << (4 * (k - 8));
                 n_total += l;
                 himask |= is_high(u) ? (1u << k) : 0u;
                 lomask |= is_low(u) ? (1u << k) : 0u;
             }
-            n_surm = (himask | lomask) & inr;
-            /* Section 3: a high unit must be followed by a low one, a low
-             * unit must follow a high one (neighbours from the halo) */
             uint64_t first_err = NONE;
-            if (n_surm) {
+            if ((himask | lomask) & inr) {
                 const uint32_t lo_next = (lomask >> 1) | (is_low(nu) ? (1u << (UPT - 1)) : 0u);   /* bit k: unit k+1 is low */
                 const uint32_t prev_hi = (himask << 1) | (is_high(pu) ? 1u : 0u);    /* bit k: unit k-1 is high */
+                /* Section 3: a high unit must be followed by a low one, a
+                 * low unit must follow a high one */
                 const uint32_t errs = ((himask & ~lo_next) | (lomask & ~prev_hi)) & inr;
                 if (errs) first_err = (uint64_t)(e0 + __ffs(errs) - 1) - head;
+                /* a pair is written whole by its high unit */
+                const uint32_t ps = himask & lo_next & inr, pe = lomask & prev_hi & inr;
+                if (ps | pe) {
+                    n_la += 2 * spread4(ps) - 2 * spread4(pe);
+                    n_lb += 2 * spread4(ps >> 8) - 2 * spread4(pe >> 8);
+                    n_total += 2 * (uint32_t)__popc(ps) - 2 * (uint32_t)__popc(pe);
+                }
             }
             bool any_err;
             n_excl = block_exclusive_or<THREADS>(n_total, first_err != NONE, s_warp, &n_total, &any_err);
@@ -343,7 +302,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             const uint16_t *sb = stages + (size_t)c_stage * Lay::STAGE_UNITS;
             const int i0 = HALO16 + tid * UPT;
             /* the look-back window's status words are requested now and
-             * examined after packing, so the round trip hides behind it */
+             * examined after the bytes are written */
             const long long lb_idx = (long long)c_tile - 1 - tid;
             const uint64_t lb_word = (c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
 
@@ -356,33 +315,14 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 w[4 * v + 2] = q.z;
                 w[4 * v + 3] = q.w;
             }
-            /* encode every unit into packed words of the staging buffer, at
-             * offsets from the tile's first output byte */
-            if (c_interior) {
-                WordPacker wp;
-                wp.start(c_excl);
+            const uint32_t nu = sb[i0 + UPT];
+            /* each unit's bytes, at offsets from the tile's first output byte */
+            uint32_t o = c_excl;
 #pragma unroll
-                for (int k = 0; k < UPT; k++) {
-                    const uint32_t u = UNIT(k);
-                    const uint32_t l = (c_lens >> (2 * k)) & 3;
-                    wp.put(outw, encode_bmp(u, l), l);
-                }
-                s_hand[tid] = wp.nbits ? wp.cur : 0u;
-                __syncthreads();
-                if (tid > 0 && (c_excl & 3)) outw[c_excl >> 2] |= s_hand[tid - 1];
-                if (tid == THREADS - 1 && wp.nbits) outw[wp.widx] = wp.cur;
-            } else {
-                for (uint32_t i = tid; i < Lay::OUT_WORDS / 4; i += THREADS) outw4[i] = make_uint4(0, 0, 0, 0);
-                __syncthreads();
-                Packer pk;
-                pk.start(c_excl);
-#pragma unroll
-                for (int k = 0; k < UPT; k++) {
-                    const uint32_t u = UNIT(k);
-                    const uint32_t l = (c_lens >> (2 * k)) & 3;
-                    pk.put(outw, l ? encode_bmp(u, l) : 0u, (int)l);
-                }
-                pk.finish(outw);
+            for (int k = 0; k < UPT; k++) {
+                const uint32_t l = ((k < 8 ? c_la >> (4 * k) : c_lb >> (4 * (k - 8)))) & 0xF;
+                put_utf8(outb, o, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
+                o += l;
             }
 
             /* the window: usable when an inclusive prefix appears in it and
@@ -398,7 +338,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 const int stop = pmask ? __ffs(pmask) - 1 : 31;
                 uint64_t v = (lane <= stop && in_window) ? (lb_word & VALUE_MASK) : 0;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
                 if (lane == 0) {
                     s_lb_sum[wid] = v;
                     s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
@@ -414,26 +354,10 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                     }
                 }
                 __syncthreads();
-                if (!(found && usable))   /* rare: fall back to polling */
+                if (!(found && usable))   /* rare: poll until the predecessors publish */
                     G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
                 if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
             } else {
-                __syncthreads();
-            }
-
-            /* surrogate units: their two bytes, once every packed word is in place */
-            if (__syncthreads_or(c_surm != 0)) {
-                uint32_t m = c_surm;
-                while (m) {
-                    const int k = __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint32_t below = c_lens & ((1u << (2 * k)) - 1);
-                    const uint32_t o = c_excl + __popc(below & 0x55555555u) + 2 * __popc(below & 0xAAAAAAAAu);
-                    uint32_t b0, b1;
-                    surrogate_bytes(sb[i0 + k], sb[i0 + k - 1], &b0, &b1);
-                    outb[o] = (uint8_t)b0;
-                    outb[o + 1] = (uint8_t)b1;
-                }
                 __syncthreads();
             }
 
@@ -450,38 +374,33 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             for (uint32_t i = tid; i < nvec; i += THREADS) {
                 const uint32_t lo = 16 * i, hi = lo + 16;
                 if (lo >= shift && hi <= lim) {
-                    const uint32_t j = 4 * i - q;   /* staging word holding the first byte's word-aligned part */
-                    uint4 o;
+                    const uint32_t j = 4 * i - q;
+                    uint4 ov;
                     if (r8 == 0) {
-                        o = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
+                        ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
                     } else {
                         const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
-                        o = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
-                                       __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
+                        ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
+                                        __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
                     }
-                    st_stream16(gbase + lo, o);
+                    st_stream16(gbase + lo, ov);
                 } else {
                     for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = outb[b - shift];
                 }
             }
 
             /* the first character whose bytes do not fit (only in the tile
-             * that crosses the capacity) */
+             * that crosses the capacity): a unit that writes bytes starts a
+             * character, and a pair needs all four */
             if (G0 <= cap && G0 + c_total > cap) {
                 const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * UPT);
                 uint64_t cap_first = NONE;
                 uint64_t g = G0 + c_excl;
-                uint32_t prev = sb[i0 - 1];
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
-                    const uint32_t u = UNIT(k);
-                    const uint32_t l = (c_lens >> (2 * k)) & 3;
-                    const uint32_t next = k + 1 < UPT ? UNIT(k + 1) : sb[i0 + UPT];
-                    const bool pair_tail = is_low(u) && is_high(prev);
-                    const uint32_t need = (is_high(u) && is_low(next)) ? 4 : l;
-                    if (l && !pair_tail && g + need > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
+                    const uint32_t l = ((k < 8 ? c_la >> (4 * k) : c_lb >> (4 * (k - 8)))) & 0xF;
+                    if (l && g + l > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
                     g += l;
-                    prev = u;
                 }
                 const uint64_t m = block_min<THREADS>(cap_first, s_min);
                 if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
@@ -493,12 +412,11 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         if (!have_n) break;
         if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
         have_c = true;
-        c_interior = interior;
         c_tile = t;
         c_total = n_total;
         c_excl = n_excl;
-        c_lens = n_lens;
-        c_surm = n_surm;
+        c_la = n_la;
+        c_lb = n_lb;
         c_stage = sn;
         __syncthreads();
     }
@@ -525,11 +443,17 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     if (error == GPUTF_E_OK) {
         written = ld_relaxed(status + tiles - 1) & VALUE_MASK;
     } else if (error != GPUTF_E_TIMEOUT) {
+        /* bytes of [0, pos): the tiles before pos's tile, then a recount
+         * with the same per-unit convention (every pair in it is complete:
+         * pos is the first error or the start of a character) */
         const uint64_t t = (head + pos) / TILE;
         const uint64_t before = t ? (ld_relaxed(status + t - 1) & VALUE_MASK) : 0;
         const uint64_t start = t * TILE > head ? t * TILE - head : 0;
         uint32_t c = 0;
-        for (uint64_t i = start + tid; i < pos; i += THREADS) c += len8(in[i]);
+        for (uint64_t i = start + tid; i < pos; i += THREADS) {
+            const uint32_t u = in[i];
+            c += (is_low(u) && i > 0 && is_high(in[i - 1])) ? 0u : (is_high(u) ? 4u : len8(u));
+        }
         uint32_t sum;
         block_exclusive<THREADS>(c, s_warp, &sum);
         written = before + sum;
@@ -656,7 +580,9 @@ cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, u
     auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES>;
     static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U16_THREADS, U16Lay::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U16Lay::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U16_THREADS, U16Lay::SMEM);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }

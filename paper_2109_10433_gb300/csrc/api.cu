@@ -121,7 +121,7 @@ gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *ou
     int sms;
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
-                                                   reinterpret_cast<gputf::DevResult *>(res), stream));
+                                                   reinterpret_cast<gputf::DevResult *>(res), sms, stream));
 }
 
 gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,

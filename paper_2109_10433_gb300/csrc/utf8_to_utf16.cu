@@ -111,148 +111,297 @@ __device__ __forceinline__ int decode_utf8(uint32_t q, uint32_t *u0, uint32_t *u
     return pair ? 2 : 1;
 }
 
-template <int THREADS, int WORDS>
+constexpr int HALO8 = 16;   /* bytes staged on each side of a tile */
+
+template <int THREADS, int WORDS, int STAGES>
+struct U8Layout {
+    static constexpr int BPT = 4 * WORDS;
+    static constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    static constexpr uint32_t STAGE_BYTES = (uint32_t)TILE + 2 * HALO8;
+    static constexpr uint32_t OUT_BYTES = (uint32_t)(4 * TILE + 32);   /* up to 2 units per byte */
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + OUT_BYTES;
+    static_assert(STAGE_BYTES % 16 == 0 && OUT_BYTES % 16 == 0, "16-byte granules");
+};
+
+/*
+ * Persistent transcoder, software-pipelined over tiles (the same schedule as
+ * the UTF-16 -> UTF-8 kernel): each iteration runs phase A of the tile n
+ * whose input just arrived (lengths, validation, block scan, aggregate) and
+ * phase B of the tile c before it (look-back, decode into the staging buffer,
+ * inclusive prefix, write-out), then takes a new ticket and starts its input
+ * copy into the stage c used.  Input arrives with 16 bytes of halo on each
+ * side: the 3 bytes before a position validate it, the 3 after complete a
+ * character that starts near the tile's end.
+ */
+template <int THREADS, int WORDS, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, DevResult *res)
+                     uint64_t status_words, uint64_t tiles, DevResult *res)
 {
-    constexpr int BPT = 4 * WORDS;
-    constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    using Lay = U8Layout<THREADS, WORDS, STAGES>;
+    constexpr int BPT = Lay::BPT;
+    constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
-    __shared__ uint32_t s_warp[WARPS + 1];
+    static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
+    extern __shared__ uint4 smem4[];
+    uint8_t *stages = reinterpret_cast<uint8_t *>(smem4);
+    uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
+    uint32_t *outw = reinterpret_cast<uint32_t *>(outw4);
+    uint16_t *out16 = reinterpret_cast<uint16_t *>(outw4);
+    uint8_t *outb = reinterpret_cast<uint8_t *>(outw4);
+    __shared__ unsigned long long s_bar[STAGES];
+    __shared__ unsigned long long s_ring[STAGES];
+    __shared__ uint32_t s_warp[WARPS + 2];
     __shared__ unsigned long long s_min[WARPS];
-    __shared__ unsigned long long s_tile_excl;
-    __shared__ unsigned s_tile, s_flag;
-    extern __shared__ uint4 s_stage4[];
-    uint16_t *stage = reinterpret_cast<uint16_t *>(s_stage4);
+    __shared__ unsigned long long s_lb_sum[WARPS];
+    __shared__ unsigned s_lb_has[WARPS];
+    __shared__ unsigned s_flag;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = (unsigned)atomicAdd(&hdr->ticket, 1ull);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
-
+    const int tid = threadIdx.x;
     const uint64_t head = (uintptr_t)in & 15;
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;    /* extended index of the end position */
-    const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
+    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
 
-    /* 1. load */
-    uint32_t w[WORDS];
-    const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
-    uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
-    uint32_t nw = __shfl_down_sync(FULL_MASK, w[0], 1);
-    if (lane == 0) pw = word_at(base, (long long)e0 - 4, head, endx);
-    if (lane == 31) nw = word_at(base, (long long)(e0 + BPT), head, endx);
-
-    /* 3. per-byte lengths: leads (non-continuation bytes) and four-byte leads */
-    uint32_t lead[WORDS], f4[WORDS];
-    uint32_t any = pw, total = 0;
-#pragma unroll
-    for (int k = 0; k < WORDS; k++) {
-        const uint32_t x = w[k];
-        any |= x;
-        lead[k] = ~(x & ~(x << 1)) & 0x80808080u;
-        f4[k] = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
-        if (!interior) {
-            const uint32_t rm = range_mask((long long)(e0 + 4 * k), head, endx, false);
-            lead[k] &= rm;
-            f4[k] &= rm;
-        }
-        total += __popc(lead[k]) + __popc(f4[k]);
-    }
-
-    /* 2. validation, skipped by all-ASCII warps and all-ASCII threads */
-    const bool ascii = (any & 0x80808080u) == 0;
-    uint64_t first_err = NONE;
-    if (!__all_sync(FULL_MASK, ascii) && !ascii) {
-#pragma unroll
-        for (int k = WORDS - 1; k >= 0; k--) {
-            uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
-            if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
-            if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
-        }
-    }
-
-    /* block scan and look-back */
-    uint32_t tile_total;
-    const uint32_t excl_local = block_exclusive<THREADS>(total, s_warp, &tile_total);
-    if (warp == 0) {
-        uint64_t excl = 0;
-        if (tile == 0) {
-            if (lane == 0) st_release(status, make_status(epoch, ST_PREFIX, tile_total));
+    auto issue = [&](unsigned long long t, int s) {
+        s_ring[s] = t;
+        if (t >= tiles) return;
+        const uint64_t x0 = t * TILE;
+        if (x0 >= head + HALO8 && x0 + TILE + HALO8 <= endx) {
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&s_bar[s], Lay::STAGE_BYTES);
+            bulk_load(stages + (size_t)s * Lay::STAGE_BYTES, base + x0 - HALO8, Lay::STAGE_BYTES, &s_bar[s]);
         } else {
-            if (lane == 0) st_release(status + tile, make_status(epoch, ST_AGGREGATE, tile_total));
-            excl = look_back(status, (long long)tile, epoch, &hdr->flags);
-            if (lane == 0) st_release(status + tile, make_status(epoch, ST_PREFIX, excl + tile_total));
+            mbar_arrive(&s_bar[s]);
         }
-        if (lane == 0) s_tile_excl = excl;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        fence_mbar_init();
+        issue(atomicAdd(&hdr->ticket, 1ull), 0);
+        issue(atomicAdd(&hdr->ticket, 1ull), 1);
     }
     __syncthreads();
-    const uint64_t G0 = s_tile_excl;
 
-    /* 4. decode into the staging buffer */
-    const uint32_t shift = (uint32_t)(((uintptr_t)(out + G0) >> 1) & 7);
-    uint32_t o = shift + excl_local;
-    uint64_t g = G0 + excl_local;
-    uint64_t cap_first = NONE;
-    if (__all_sync(FULL_MASK, ascii)) {
+    bool have_c = false, c_interior = false;
+    unsigned long long c_tile = 0;
+    uint32_t c_total = 0, c_excl = 0;
+    int c_stage = 0;
+
+    for (int it = 0;; it++) {
+        /* ---------------- phase A of tile n ---------------- */
+        const int sn = it % STAGES;
+        const unsigned long long t = s_ring[sn];
+        const bool have_n = t < tiles;
+        const uint64_t x0n = t * TILE;
+        const bool interior = have_n && x0n >= head + HALO8 && x0n + TILE + HALO8 <= endx;
+        uint32_t n_total = 0, n_excl = 0;
+        if (have_n) {
+            uint8_t *sb = stages + (size_t)sn * Lay::STAGE_BYTES;
+            if (interior) {
+                if (!mbar_wait(&s_bar[sn], (uint32_t)((it / STAGES) & 1))) atomicOr(&hdr->flags, FLAG_TIMEOUT);
+            } else {
+                for (int i = tid; i < (int)Lay::STAGE_BYTES; i += THREADS)
+                    sb[i] = (uint8_t)byte_at(base, (long long)(x0n + i) - HALO8, head, endx);
+                __syncthreads();
+            }
+            const int i0 = HALO8 + tid * BPT;
+            const long long e0 = (long long)(x0n + (uint64_t)tid * BPT);
+            uint32_t w[WORDS];
 #pragma unroll
-        for (int k = 0; k < WORDS; k++) {
+            for (int v = 0; v < WORDS / 4; v++) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 16 * v);
+                w[4 * v + 0] = q.x;
+                w[4 * v + 1] = q.y;
+                w[4 * v + 2] = q.z;
+                w[4 * v + 3] = q.w;
+            }
+            const uint32_t pw = *reinterpret_cast<const uint32_t *>(sb + i0 - 4);
+            /* per-byte output units: leads (non-continuation bytes) count 1,
+             * four-byte leads 2 */
+            uint32_t any = pw;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (lead[k] & (0x80u << (8 * j))) {
-                    stage[o] = (uint16_t)((w[k] >> (8 * j)) & 0xFF);
-                    if (g >= cap && cap_first == NONE) cap_first = e0 + 4 * k + j - head;
-                    o++;
-                    g++;
+            for (int k = 0; k < WORDS; k++) {
+                const uint32_t x = w[k];
+                any |= x;
+                uint32_t lead = ~(x & ~(x << 1)) & 0x80808080u;
+                uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
+                if (!interior) {
+                    const uint32_t rm = range_mask(e0 + 4 * k, head, endx, false);
+                    lead &= rm;
+                    f4 &= rm;
+                }
+                n_total += __popc(lead) + __popc(f4);
+            }
+            /* validation, skipped by all-ASCII warps and all-ASCII threads */
+            const bool ascii = (any & 0x80808080u) == 0;
+            uint64_t first_err = NONE;
+            if (!__all_sync(FULL_MASK, ascii) && !ascii) {
+#pragma unroll
+                for (int k = WORDS - 1; k >= 0; k--) {
+                    uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
+                    if (!interior) nz &= range_mask(e0 + 4 * k, head, endx, true);
+                    if (nz) first_err = (uint64_t)(e0 + 4 * k + first_byte(nz)) - head;
                 }
             }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < WORDS; k++) {
-            const uint32_t nxt = k + 1 < WORDS ? w[k + 1] : nw;
-            uint32_t m = lead[k];
-            while (m) {
-                const int j = first_byte(m);
-                m &= m - 1;
-                const uint32_t q = gputf_fshr(w[k], nxt, 8 * j);
-                uint32_t u0, u1;
-                const int c = decode_utf8(q, &u0, &u1);
-                stage[o] = (uint16_t)u0;
-                if (c == 2) stage[o + 1] = (uint16_t)u1;
-                if (g + c > cap && cap_first == NONE) cap_first = e0 + 4 * k + j - head;
-                o += c;
-                g += c;
+            bool any_err;
+            n_excl = block_exclusive_or<THREADS>(n_total, first_err != NONE, s_warp, &n_total, &any_err);
+            if (tid == 0)
+                st_release(status + t, make_status(epoch, t == 0 ? ST_PREFIX : ST_AGGREGATE, n_total));
+            if (any_err) {
+                const uint64_t m = block_min<THREADS>(first_err, s_min);
+                if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
             }
         }
-    }
 
-    /* 5. first error and first character that does not fit */
-    if (__syncthreads_or(first_err != NONE)) {
-        const uint64_t m = block_min<THREADS>(first_err, s_min);
-        if (tid == 0) atomicMin(&hdr->err_pos, (unsigned long long)m);
-    }
-    if (G0 <= cap && G0 + tile_total > cap) {
-        const uint64_t m = block_min<THREADS>(cap_first, s_min);
-        if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
-    }
-    __syncthreads();
+        /* ---------------- look-back and phase B of tile c ---------------- */
+        if (have_c) {
+            const uint8_t *sb = stages + (size_t)c_stage * Lay::STAGE_BYTES;
+            const int i0 = HALO8 + tid * BPT;
+            const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * BPT);
+            const long long lb_idx = (long long)c_tile - 1 - tid;
+            const uint64_t lb_word = (c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
 
-    /* write the tile's output range [G0, G0 + cnt), clipped to the capacity */
-    uint64_t cnt = G0 >= cap ? 0 : (G0 + tile_total > cap ? cap - G0 : tile_total);
-    uint16_t *gbase = out + G0 - shift;     /* 16-byte aligned; index 0 <-> stage[0] */
-    const uint32_t lim = shift + (uint32_t)cnt;
-    const uint32_t nvec = (lim + 7) / 8;
-    for (uint32_t i = tid; i < nvec; i += THREADS) {
-        const uint32_t lo = 8 * i, hi = lo + 8;
-        if (lo >= shift && hi <= lim) {
-            st_stream16(gbase + lo, s_stage4[i]);
-        } else {
-            for (uint32_t u = lo < shift ? shift : lo; u < (hi < lim ? hi : lim); u++) gbase[u] = stage[u];
+            uint32_t w[WORDS];
+#pragma unroll
+            for (int v = 0; v < WORDS / 4; v++) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 16 * v);
+                w[4 * v + 0] = q.x;
+                w[4 * v + 1] = q.y;
+                w[4 * v + 2] = q.z;
+                w[4 * v + 3] = q.w;
+            }
+            const uint32_t nw = *reinterpret_cast<const uint32_t *>(sb + i0 + BPT);
+            uint32_t lead[WORDS], any = 0;
+#pragma unroll
+            for (int k = 0; k < WORDS; k++) {
+                const uint32_t x = w[k];
+                any |= x;
+                lead[k] = ~(x & ~(x << 1)) & 0x80808080u;
+                if (!c_interior) lead[k] &= range_mask(e0 + 4 * k, head, endx, false);
+            }
+            /* decode at every lead into the staging buffer, in units from the
+             * tile's first output unit (Section 3 bit arithmetic; Figs. 2-4) */
+            uint32_t o = c_excl;
+            if (__all_sync(FULL_MASK, (any & 0x80808080u) == 0)) {
+#pragma unroll
+                for (int k = 0; k < WORDS; k++) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (lead[k] & (0x80u << (8 * j))) out16[o++] = (uint16_t)((w[k] >> (8 * j)) & 0xFF);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < WORDS; k++) {
+                    const uint32_t nxt = k + 1 < WORDS ? w[k + 1] : nw;
+                    uint32_t m = lead[k];
+                    while (m) {
+                        const int j = first_byte(m);
+                        m &= m - 1;
+                        uint32_t u0, u1;
+                        const int c = decode_utf8(gputf_fshr(w[k], nxt, 8 * j), &u0, &u1);
+                        out16[o] = (uint16_t)u0;
+                        if (c == 2) out16[o + 1] = (uint16_t)u1;
+                        o += c;
+                    }
+                }
+            }
+
+            uint64_t G0 = 0;
+            if (c_tile > 0) {
+                const bool in_window = lb_idx >= 0;
+                const uint64_t flag = in_window ? ((lb_word >> 40) & 3) : ST_PREFIX;
+                const bool ok = !in_window || ((unsigned)(lb_word >> 42) == epoch && flag != 0);
+                const unsigned pmask = __ballot_sync(FULL_MASK, ok && flag == ST_PREFIX);
+                const unsigned bad = __ballot_sync(FULL_MASK, !ok);
+                const int lane = tid & 31, wid = tid >> 5;
+                const int stop = pmask ? __ffs(pmask) - 1 : 31;
+                uint64_t v = (lane <= stop && in_window) ? (lb_word & VALUE_MASK) : 0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+                if (lane == 0) {
+                    s_lb_sum[wid] = v;
+                    s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
+                }
+                __syncthreads();
+                bool found = false, usable = true;
+#pragma unroll
+                for (int k = 0; k < WARPS; k++) {
+                    if (!found && usable) {
+                        usable = (s_lb_has[k] & 2u) == 0;
+                        G0 += s_lb_sum[k];
+                        found = (s_lb_has[k] & 1u) != 0;
+                    }
+                }
+                __syncthreads();
+                if (!(found && usable))
+                    G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
+                if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
+            } else {
+                __syncthreads();
+            }
+
+            /* write the tile's units [G0, G0 + cnt), clipped to the capacity,
+             * with aligned 16-byte stores assembled by funnel shifts */
+            const uint64_t cnt = G0 >= cap ? 0 : (G0 + c_total > cap ? cap - G0 : c_total);
+            const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
+            uint8_t *gbase = reinterpret_cast<uint8_t *>(out + G0) - shift;
+            const uint32_t lim = shift + 2 * (uint32_t)cnt;
+            const uint32_t nvec = (lim + 15) / 16;
+            const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
+            for (uint32_t i = tid; i < nvec; i += THREADS) {
+                const uint32_t lo = 16 * i, hi = lo + 16;
+                if (lo >= shift && hi <= lim) {
+                    const uint32_t j = 4 * i - q;
+                    uint4 ov;
+                    if (r8 == 0) {
+                        ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
+                    } else {
+                        const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
+                        ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
+                                        __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
+                    }
+                    st_stream16(gbase + lo, ov);
+                } else {
+                    for (uint32_t b = (lo < shift ? shift : lo); b < (hi < lim ? hi : lim); b += 2)
+                        *reinterpret_cast<uint16_t *>(gbase + b) = *reinterpret_cast<const uint16_t *>(outb + b - shift);
+                }
+            }
+
+            /* the first character whose units do not fit (only in the tile
+             * that crosses the capacity) */
+            if (G0 <= cap && G0 + c_total > cap) {
+                uint64_t cap_first = NONE;
+                uint64_t g = G0 + c_excl;
+#pragma unroll
+                for (int k = 0; k < WORDS; k++) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (lead[k] & (0x80u << (8 * j))) {
+                            const uint32_t c = ((w[k] >> (8 * j)) & 0xFF) >= 0xF0 ? 2u : 1u;
+                            if (g + c > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + 4 * k + j) - head;
+                            g += c;
+                        }
+                    }
+                }
+                const uint64_t m = block_min<THREADS>(cap_first, s_min);
+                if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
+            }
+            __syncthreads();
         }
+
+        if (!have_n) break;
+        if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
+        have_c = true;
+        c_interior = interior;
+        c_tile = t;
+        c_total = n_total;
+        c_excl = n_excl;
+        c_stage = sn;
+        __syncthreads();
     }
 
     /* the CTA that finishes last writes the result */
@@ -281,7 +430,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     }
     uint64_t written = 0;
     if (error == GPUTF_E_OK) {
-        written = ld_relaxed(status + gridDim.x - 1) & VALUE_MASK;
+        written = ld_relaxed(status + tiles - 1) & VALUE_MASK;
     } else if (error != GPUTF_E_TIMEOUT) {
         /* output units of [0, pos): earlier tiles' total plus a recount */
         const uint64_t t = (head + pos) / TILE;
@@ -404,23 +553,35 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
  * ---------------------------------------------------------------------- */
 constexpr int U8_THREADS = 256;
 constexpr int U8_WORDS = 4;     /* 16 bytes per thread, 4 KiB tiles */
-constexpr uint64_t U8_TILE = (uint64_t)U8_THREADS * 4 * U8_WORDS;
+constexpr int U8_STAGES = 3;
+using U8Lay = U8Layout<U8_THREADS, U8_WORDS, U8_STAGES>;
 
 uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
 {
-    return ((uintptr_t)in % 16 + n + 1 + U8_TILE - 1) / U8_TILE;
+    /* tiles cover the end position n as well (a character cut short there is
+     * flagged at n) */
+    return ((uintptr_t)in % 16 + n + 1 + U8Lay::TILE - 1) / U8Lay::TILE;
 }
 
 cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
-                                 void *ws, uint64_t status_words, DevResult *res,
+                                 void *ws, uint64_t status_words, DevResult *res, int sms,
                                  cudaStream_t stream)
 {
+    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U8Lay::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, U8_THREADS, U8Lay::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
     const uint64_t tiles = utf8_to_utf16_tiles(in, n);
-    const size_t smem = (2 * U8_TILE + 8) * sizeof(uint16_t);
+    const uint64_t grid = tiles < (uint64_t)sms * per_sm ? tiles : (uint64_t)sms * per_sm;
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
-    utf8_to_utf16_kernel<U8_THREADS, U8_WORDS><<<(unsigned)tiles, U8_THREADS, smem, stream>>>(
-        in, n, out, cap, hdr, status, status_words, res);
+    kern<<<(unsigned)grid, U8_THREADS, U8Lay::SMEM, stream>>>(in, n, out, cap, hdr, status, status_words,
+                                                              tiles, res);
     return cudaGetLastError();
 }
 

@@ -155,6 +155,45 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream);
 
+/* One direction of a batch: `count` strings stored back to back.
+ *   in, in_offsets : device; string s is in[in_offsets[s] .. in_offsets[s+1])
+ *                    in code units of its encoding (bytes, or 16-bit units on
+ *                    a 2-byte aligned buffer); count + 1 non-decreasing
+ *                    offsets starting at 0; empty strings are allowed;
+ *   units          : in_offsets[count], given here so that no device read is
+ *                    needed to size the launch;
+ *   out, out_offsets : device; string s may write output code units
+ *                    out[out_offsets[s] .. out_offsets[s+1]) (its capacity);
+ *   results        : device; count results, as gputf_result for a single
+ *                    string, positions and `written` relative to the string. */
+typedef struct gputf_batch {
+    uint64_t count;
+    uint64_t units;
+    const void *in;
+    const uint64_t *in_offsets;
+    void *out;
+    const uint64_t *out_offsets;
+    gputf_result *results;
+} gputf_batch;
+
+/* Workspace bytes for a batch with the given input units and strings per
+ * direction (UTF-8 -> UTF-16, then UTF-16 -> UTF-8). */
+size_t gputf_batch_workspace_bytes(uint64_t units8, uint64_t count8, uint64_t units16, uint64_t count16);
+
+/* Number of tile configurations gputf_batch_transcode accepts (0 .. n-1);
+ * an autotuner picks one per input mix. */
+int gputf_batch_config_count(void);
+
+/* Batched validating transcoding of many strings in one launch (the paper's
+ * single-string transcoders of Sections 4-5 applied to every string; tiles
+ * of the launch cross string boundaries).  Either direction may be NULL or
+ * have count 0.  Each string gets exactly the result and output that the
+ * single-string call would give it.  `config` selects the tile shape.
+ * Enqueued on `stream`; allocates nothing, so it can be captured into a CUDA
+ * graph. */
+gputf_status gputf_batch_transcode(const gputf_batch *utf8_to_utf16, const gputf_batch *utf16_to_utf8,
+                                   int config, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Largest input, in 16-bit units, that gputf_utf16_to_utf8_static accepts
  * (32 Mi units, 64 MiB of UTF-16). */
 #define GPUTF_STATIC_MAX_UNITS (((uint64_t)1) << 25)

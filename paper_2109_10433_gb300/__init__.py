@@ -53,6 +53,9 @@ SIGNATURES = {
     "gputf_utf8_to_utf16_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_static": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_batch_workspace_bytes": ([ctypes.c_uint64] * 4, _S),
+    "gputf_batch_config_count": ([], _I),
+    "gputf_batch_transcode": ([_P, _P, _I, _P, _S, _P], _I),
     "gputf_error_name": ([ctypes.c_int32], ctypes.c_char_p),
     "gputf_status_name": ([_I], ctypes.c_char_p),
     "gputf_last_cuda_error": ([], _I),
@@ -141,6 +144,17 @@ class Workspace:
                                device=device if device is not None else "cuda")
         _check(lib().gputf_workspace_init(_ptr(self.buf), self.nbytes, _stream(stream)),
                "gputf_workspace_init")
+
+    @classmethod
+    def of_bytes(cls, nbytes: int, device=None, stream=None):
+        """A workspace of exactly `nbytes` (for example gputf_batch_workspace_bytes)."""
+        torch = _torch()
+        ws = cls.__new__(cls)
+        ws.max_units = 0
+        ws.nbytes = int(nbytes)
+        ws.buf = torch.empty(ws.nbytes, dtype=torch.uint8, device=device if device is not None else "cuda")
+        _check(lib().gputf_workspace_init(_ptr(ws.buf), ws.nbytes, _stream(stream)), "gputf_workspace_init")
+        return ws
 
     @property
     def ptr(self):

@@ -231,6 +231,47 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
     return cuda_status(cudaStreamSynchronize(stream));
 }
 
+size_t gputf_batch_workspace_bytes(uint64_t units8, uint64_t count8, uint64_t units16, uint64_t count16)
+{
+    const uint64_t t = gputf::batch_min_tile_units();
+    const uint64_t tiles = (units8 + t - 1) / t + 1 + (units16 + t - 1) / t + 1;
+    return gputf::HEADER_BYTES + 8 * (tiles + count8 + count16);
+}
+
+int gputf_batch_config_count(void) { return gputf::batch_config_count(); }
+
+gputf_status gputf_batch_transcode(const gputf_batch *b8, const gputf_batch *b16, int config, void *ws,
+                                   size_t ws_bytes, cudaStream_t stream)
+{
+    gputf::BatchDir d[2] = {};
+    const gputf_batch *b[2] = {b8, b16};
+    for (int k = 0; k < 2; k++) {
+        if (b[k] == nullptr || b[k]->count == 0) continue;
+        const gputf_batch &x = *b[k];
+        if (x.in_offsets == nullptr || x.out_offsets == nullptr || x.results == nullptr ||
+            (x.units > 0 && x.in == nullptr) || !aligned(x.results, 8) || !aligned(x.in_offsets, 8) ||
+            !aligned(x.out_offsets, 8) || (k == 1 && !aligned(x.in, 2)) || (k == 0 && !aligned(x.out, 2)))
+            return GPUTF_STATUS_INVALID_ARGUMENT;
+        if (x.units > GPUTF_MAX_UNITS) return GPUTF_STATUS_INPUT_TOO_LARGE;
+        d[k].count = x.count;
+        d[k].units = x.units;
+        d[k].in = x.in;
+        d[k].in_off = x.in_offsets;
+        d[k].out = x.out;
+        d[k].out_off = x.out_offsets;
+        d[k].res = reinterpret_cast<gputf::DevResult *>(x.results);
+    }
+    if (config < 0) config = 0;
+    if (config >= gputf::batch_config_count() || ws == nullptr || !aligned(ws, 16))
+        return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (ws_bytes < gputf_batch_workspace_bytes(d[0].units, d[0].count, d[1].units, d[1].count))
+        return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    int sms;
+    gputf_status st = current_device(&sms);
+    if (st != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_batch(config, d[0], d[1], ws, (ws_bytes - gputf::HEADER_BYTES) / 8, stream));
+}
+
 const char *gputf_error_name(int32_t error)
 {
     static const char *names[] = {"OK",        "HEADER_BITS", "TOO_SHORT",        "TOO_LONG",

@@ -1,0 +1,703 @@
+/*
+ * Batched transcoding: many strings of uneven lengths, given as CSR offsets,
+ * in one launch whose tiles cross string boundaries.
+ *
+ * For each direction, the strings are the consecutive pieces of one input
+ * buffer, in_offsets[s] .. in_offsets[s + 1], and string s writes its output
+ * into out[out_offsets[s] .. out_offsets[s + 1]) (its capacity) and its
+ * result into results[s].  Tiles of that buffer are taken in ticket order by
+ * one grid that serves both directions (UTF-8 tiles first).
+ *
+ * Output offsets inside each string come from a segmented scan: per tile,
+ * the block scans (starts-a-string, sum) pairs, and the tile's carry into
+ * the string it begins inside comes from a segmented decoupled look-back
+ * (a walk back that stops at an inclusive prefix or at a tile in which a
+ * string starts).  Validation follows the strings' edges: a string's first
+ * units do not see the units before it, and a UTF-8 character cut short by
+ * the string's end is flagged at the end.  The tile that holds a string's
+ * last unit writes its result; errors and overflowing capacities are then
+ * finished by that thread with the scalar steps of the single-buffer path.
+ */
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gputf {
+
+/* Segmented status word: epoch (21) | starts-a-string (1) | flag (2) | value (40). */
+constexpr unsigned SEG_EPOCH_BITS = 21;
+constexpr unsigned SEG_EPOCH_MASK = (1u << SEG_EPOCH_BITS) - 1;
+
+__device__ __forceinline__ uint64_t seg_status(unsigned epoch, uint64_t flag, bool start, uint64_t value)
+{
+    return ((uint64_t)(epoch & SEG_EPOCH_MASK) << 43) | ((uint64_t)start << 42) | (flag << 40) |
+           (value & VALUE_MASK);
+}
+
+/* Per-string error words: (epoch << 40) | (VALUE_MASK - position), combined
+ * with atomicMax, so the smallest position of the current call wins and
+ * words from earlier calls (smaller epochs) never read as current. */
+__device__ __forceinline__ void record_string_error(unsigned long long *errw, uint64_t s, unsigned epoch,
+                                                    uint64_t pos)
+{
+    atomicMax(errw + s, ((unsigned long long)epoch << 40) | (VALUE_MASK - pos));
+}
+
+__device__ __forceinline__ uint64_t string_error(const unsigned long long *errw, uint64_t s, unsigned epoch)
+{
+    const uint64_t w = ld_relaxed(errw + s);
+    return (unsigned)(w >> 40) == epoch ? VALUE_MASK - (w & VALUE_MASK) : NONE;
+}
+
+constexpr int BATCH_OFF_CACHE = 512;   /* string offsets cached per tile */
+
+struct BatchShared {
+    unsigned long long off[BATCH_OFF_CACHE];
+    unsigned long long s_first;
+    unsigned n_cached;
+    uint32_t warp_f[33];
+    unsigned long long warp_v[33];
+    unsigned long long lb_sum[32];
+    unsigned lb_has[32];
+    unsigned long long carry;
+};
+
+/* in_off[s], from the tile's cache when it holds it. */
+__device__ __forceinline__ uint64_t off_at(const BatchDir &d, const BatchShared &sm, uint64_t s)
+{
+    const uint64_t j = s - sm.s_first;
+    return j < sm.n_cached ? sm.off[j] : d.in_off[s];
+}
+
+/* Warp 0: the last string s with in_off[s] <= x (the one containing unit x
+ * when it is not empty), then the offsets from there to the first one at or
+ * past x_end: the first BATCH_OFF_CACHE go into the cache, and every empty
+ * string starting in [x, x_end) gets its result here. */
+__device__ void find_strings(const BatchDir &d, BatchShared &sm, uint64_t x, uint64_t x_end)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t lo = 0, hi = d.count;   /* answer in [lo, hi]; in_off[lo] <= x */
+    while (hi - lo > 31) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t probe = lo + step * lane;
+        const bool le = probe <= hi && d.in_off[probe] <= x;
+        const unsigned m = __ballot_sync(FULL_MASK, le);
+        const uint64_t nlo = lo + step * (31 - __clz(m));
+        hi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+    }
+    {
+        const uint64_t probe = lo + lane;
+        const bool le = probe <= hi && d.in_off[probe] <= x;
+        const unsigned m = __ballot_sync(FULL_MASK, le);
+        lo = lo + (31 - __clz(m));
+    }
+    const uint64_t s_first = lo < d.count ? lo : (d.count ? d.count - 1 : 0);
+    if (lane == 0) sm.s_first = s_first;
+    uint64_t n = 0;
+    for (;;) {
+        const uint64_t s = s_first + n + lane;
+        const bool have = s <= d.count;
+        const uint64_t v = have ? d.in_off[s] : ~0ull;
+        if (have && n + lane < BATCH_OFF_CACHE) sm.off[n + lane] = v;
+        if (have && s < d.count && v >= x && v < x_end && d.in_off[s + 1] == v) {
+            d.res[s].error = GPUTF_E_OK;
+            d.res[s].reserved = 0;
+            d.res[s].position = 0;
+            d.res[s].written = 0;
+        }
+        const unsigned beyond = __ballot_sync(FULL_MASK, !have || v >= x_end);
+        const unsigned havem = __ballot_sync(FULL_MASK, have);
+        if (beyond) {
+            const int fb = __ffs(beyond) - 1;
+            n += fb + ((havem >> fb) & 1u);   /* keep the first offset at or past x_end */
+            break;
+        }
+        n += 32;
+    }
+    if (lane == 0) sm.n_cached = (unsigned)(n < BATCH_OFF_CACHE ? n : BATCH_OFF_CACHE);
+}
+
+/* Segmented block scan: each thread gives (f = a string starts in its
+ * chunk, v = sum after its last start, or its whole sum).  Returns the
+ * thread's exclusive pair within the tile, and the tile's aggregate. */
+template <int THREADS>
+__device__ void block_seg_scan(bool f, uint64_t v, BatchShared &sm, bool *ef, uint64_t *ev, bool *tf, uint64_t *tv)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool fi = f;
+    uint64_t vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const bool fo = __shfl_up_sync(FULL_MASK, (int)fi, o);
+        const uint64_t vo = __shfl_up_sync(FULL_MASK, vi, o);
+        if (lane >= o) {
+            vi = fi ? vi : vo + vi;
+            fi = fi || fo;
+        }
+    }
+    /* lane's exclusive within the warp */
+    bool fx = __shfl_up_sync(FULL_MASK, (int)fi, 1);
+    uint64_t vx = __shfl_up_sync(FULL_MASK, vi, 1);
+    if (lane == 0) {
+        fx = false;
+        vx = 0;
+    }
+    if (lane == 31) {
+        sm.warp_f[warp] = fi;
+        sm.warp_v[warp] = vi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bool wf = lane < WARPS ? sm.warp_f[lane] != 0 : false;
+        uint64_t wv = lane < WARPS ? sm.warp_v[lane] : 0;
+        bool pf = wf;
+        uint64_t pv = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const bool fo = __shfl_up_sync(FULL_MASK, (int)pf, o);
+            const uint64_t vo = __shfl_up_sync(FULL_MASK, pv, o);
+            if (lane >= o) {
+                pv = pf ? pv : vo + pv;
+                pf = pf || fo;
+            }
+        }
+        /* exclusive per warp, and the tile's inclusive total */
+        bool xf = __shfl_up_sync(FULL_MASK, (int)pf, 1);
+        uint64_t xv = __shfl_up_sync(FULL_MASK, pv, 1);
+        if (lane == 0) {
+            xf = false;
+            xv = 0;
+        }
+        if (lane < WARPS) {
+            sm.warp_f[lane] = xf;
+            sm.warp_v[lane] = xv;
+        }
+        if (lane == WARPS - 1) {
+            sm.warp_f[32] = pf;
+            sm.warp_v[32] = pv;
+        }
+    }
+    __syncthreads();
+    const bool wf = sm.warp_f[warp] != 0;
+    const uint64_t wv = sm.warp_v[warp];
+    /* combine the warp's exclusive with the lane's */
+    *ev = fx ? vx : wv + vx;
+    *ef = wf || fx;
+    *tf = sm.warp_f[32] != 0;
+    *tv = sm.warp_v[32];
+    __syncthreads();
+}
+
+/* Segmented look-back: the sum carried into tile t from the string it
+ * begins inside.  All threads; returns the value to every thread. */
+template <int THREADS>
+__device__ uint64_t block_seg_look_back(unsigned long long *status, long long tile, unsigned epoch,
+                                        unsigned *flags, BatchShared &sm)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t carry = 0;
+    long long end = tile - 1;
+    while (end >= 0) {
+        const long long idx = end - threadIdx.x;
+        bool stop = true;
+        uint64_t value = 0;
+        if (idx >= 0) {
+            int spins = 0;
+            unsigned ns = 32;
+            while (true) {
+                const uint64_t w = ld_acquire(status + idx);
+                const uint64_t fl = (w >> 40) & 3;
+                if ((unsigned)(w >> 43) == (epoch & SEG_EPOCH_MASK) && fl != 0) {
+                    stop = fl == ST_PREFIX || ((w >> 42) & 1);
+                    value = w & VALUE_MASK;
+                    break;
+                }
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    stop = true;
+                    value = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        const unsigned pmask = __ballot_sync(FULL_MASK, stop);
+        const int st = pmask ? __ffs(pmask) - 1 : 31;
+        uint64_t v = lane <= st ? value : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        if (lane == 0) {
+            sm.lb_sum[warp] = v;
+            sm.lb_has[warp] = pmask != 0;
+        }
+        __syncthreads();
+        uint64_t add = 0;
+        bool found = false;
+#pragma unroll
+        for (int k = 0; k < WARPS; k++) {
+            if (!found) {
+                add += sm.lb_sum[k];
+                found = sm.lb_has[k] != 0;
+            }
+        }
+        __syncthreads();
+        carry += add;
+        if (found) break;
+        end -= THREADS;
+    }
+    return carry;
+}
+
+/* ------------------------------------------------------------------------
+ * UTF-16 -> UTF-8 tiles.
+ * ---------------------------------------------------------------------- */
+__device__ __forceinline__ bool is_hi16(uint32_t u) { return (u & 0xFC00) == 0xD800; }
+__device__ __forceinline__ bool is_lo16(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
+__device__ __forceinline__ uint32_t len8_of(uint32_t u)
+{
+    return u < 0x80 ? 1u : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2u : 3u);
+}
+
+/* Bytes unit i of a string writes (string-local neighbours prev / next,
+ * 0 outside the string): a pair is written whole by its high unit. */
+__device__ __forceinline__ uint32_t bytes16(uint32_t u, uint32_t prev, uint32_t next)
+{
+    if (is_lo16(u) && is_hi16(prev)) return 0;
+    if (is_hi16(u) && is_lo16(next)) return 4;
+    return len8_of(u);
+}
+
+__device__ __forceinline__ void put_bytes16(uint8_t *dst, uint32_t u, uint32_t next, uint32_t l)
+{
+    if (l == 1) {
+        dst[0] = (uint8_t)u;
+    } else if (l == 2) {
+        dst[0] = (uint8_t)(0xC0 | ((u >> 6) & 0x1F));
+        dst[1] = (uint8_t)(0x80 | (u & 0x3F));
+    } else if (l == 3) {
+        dst[0] = (uint8_t)(0xE0 | (u >> 12));
+        dst[1] = (uint8_t)(0x80 | ((u >> 6) & 0x3F));
+        dst[2] = (uint8_t)(0x80 | (u & 0x3F));
+    } else if (l == 4) {
+        const uint32_t c = (u << 10) + next - 0x35FDC00u;
+        dst[0] = (uint8_t)(0xF0 | (c >> 18));
+        dst[1] = (uint8_t)(0x80 | ((c >> 12) & 0x3F));
+        dst[2] = (uint8_t)(0x80 | ((c >> 6) & 0x3F));
+        dst[3] = (uint8_t)(0x80 | (c & 0x3F));
+    }
+}
+
+/* Scalar finish of string s (error and/or capacity), by one thread. */
+__device__ void finish_string16(const BatchDir &d, uint64_t s, uint64_t first_err, uint64_t total)
+{
+    const uint16_t *in = static_cast<const uint16_t *>(d.in) + d.in_off[s];
+    const uint64_t n = d.in_off[s + 1] - d.in_off[s];
+    const uint64_t cap = d.out_off[s + 1] - d.out_off[s];
+    int32_t error = GPUTF_E_OK;
+    uint64_t pos = n, written = total;
+    uint64_t g = 0;
+    /* walk characters up to the first error, stopping at the first one that
+     * does not fit */
+    for (uint64_t i = 0; i < n; i++) {
+        if (first_err != NONE && i == first_err) {
+            error = GPUTF_E_SURROGATE;
+            pos = i;
+            written = g;
+            break;
+        }
+        const uint32_t u = in[i];
+        const uint32_t prev = i ? in[i - 1] : 0u;
+        const uint32_t next = i + 1 < n ? in[i + 1] : 0u;
+        const uint32_t l = bytes16(u, prev, next);
+        if (l && g + l > cap) {
+            error = GPUTF_E_OUTPUT_TOO_SMALL;
+            pos = i;
+            written = g;
+            break;
+        }
+        g += l;
+    }
+    d.res[s].error = error;
+    d.res[s].reserved = 0;
+    d.res[s].position = pos;
+    d.res[s].written = written;
+}
+
+template <int THREADS, int UPT>
+__device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHeader *hdr, BatchShared &sm,
+                             uint16_t *stage)
+{
+    constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
+    constexpr int HALO = 8;
+    const uint16_t *in = static_cast<const uint16_t *>(d.in);
+    uint8_t *out = static_cast<uint8_t *>(d.out);
+    const int tid = threadIdx.x;
+    const uint64_t x0 = t * TILE;
+    const uint64_t x1 = x0 + TILE < d.units ? x0 + TILE : d.units;
+
+    if (tid < 32) find_strings(d, sm, x0, t + 1 == d.tiles ? ~0ull : x1);
+    for (int i = tid; i < (int)TILE + 2 * HALO; i += THREADS) {
+        const long long x = (long long)x0 + i - HALO;
+        stage[i] = (x >= 0 && (uint64_t)x < d.units) ? in[x] : 0;
+    }
+    __syncthreads();
+
+    /* this thread's units [c0, c1) and the string holding c0 */
+    const uint64_t c0 = x0 + (uint64_t)tid * UPT;
+    const uint64_t c1 = c0 + UPT < x1 ? c0 + UPT : (x1 > c0 ? x1 : c0);
+    uint64_t s;
+    {
+        /* binary search among the cached offsets (the walk steps on past
+         * the cache through in_off when a tile holds more strings) */
+        uint64_t lo = 0, hi = sm.n_cached;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (sm.off[mid] <= c0) lo = mid;
+            else hi = mid;
+        }
+        s = sm.s_first + lo;
+    }
+#define U16AT(x) ((uint32_t)stage[(x) - x0 + HALO])
+    /* phase A: bytes per unit, starts, errors */
+    bool f = false;
+    uint64_t v = 0;
+    if (c0 < c1) {
+        uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        uint64_t err_s = NONE, err_p = NONE;
+        for (uint64_t i = c0; i < c1; i++) {
+            while (i >= en) {
+                ss++;
+                st = en;
+                en = off_at(d, sm, ss + 1);
+            }
+            if (i == st) {
+                f = true;
+                v = 0;
+            }
+            const uint32_t u = U16AT(i);
+            const uint32_t prev = i > st ? U16AT(i - 1) : 0u;
+            const uint32_t next = i + 1 < en ? U16AT(i + 1) : 0u;
+            v += bytes16(u, prev, next);
+            const bool bad = (is_hi16(u) && !is_lo16(next)) || (is_lo16(u) && !is_hi16(prev));
+            if (bad && err_s != ss) {
+                record_string_error(d.errw, ss, epoch, i - st);
+                err_s = ss;
+                err_p = i;
+            }
+        }
+        (void)err_p;
+    }
+    bool ef, tf;
+    uint64_t ev, tv;
+    block_seg_scan<THREADS>(f, v, sm, &ef, &ev, &tf, &tv);
+    if (tid == 0) {
+        __threadfence();
+        st_release(d.status + t, seg_status(epoch, t == 0 ? ST_PREFIX : ST_AGGREGATE, tf, tv));
+    }
+    uint64_t carry = 0;
+    if (t > 0) carry = block_seg_look_back<THREADS>(d.status, (long long)t, epoch, &hdr->flags, sm);
+    if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
+    __threadfence();
+
+    /* phase B: bytes out, results of strings ending here */
+    if (c0 < c1) {
+        uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        uint64_t g = ef ? ev : carry + ev;   /* output position within the string */
+        uint64_t ob = d.out_off[ss], oc = d.out_off[ss + 1] - ob;
+        for (uint64_t i = c0; i < c1; i++) {
+            while (i >= en) {
+                ss++;
+                st = en;
+                en = off_at(d, sm, ss + 1);
+                ob = d.out_off[ss];
+                oc = d.out_off[ss + 1] - ob;
+            }
+            if (i == st) g = 0;
+            const uint32_t u = U16AT(i);
+            const uint32_t prev = i > st ? U16AT(i - 1) : 0u;
+            const uint32_t next = i + 1 < en ? U16AT(i + 1) : 0u;
+            const uint32_t l = bytes16(u, prev, next);
+            if (l && g + l <= oc) put_bytes16(out + ob + g, u, next, l);
+            g += l;
+            if (i + 1 == en) {   /* the string's last unit: its result */
+                const uint64_t e = string_error(d.errw, ss, epoch);
+                if (e == NONE && g <= oc) {
+                    d.res[ss].error = GPUTF_E_OK;
+                    d.res[ss].reserved = 0;
+                    d.res[ss].position = en - st;
+                    d.res[ss].written = g;
+                } else {
+                    finish_string16(d, ss, e, g);
+                }
+            }
+        }
+    }
+#undef U16AT
+    __syncthreads();
+}
+
+/* ------------------------------------------------------------------------
+ * UTF-8 -> UTF-16 tiles.
+ * ---------------------------------------------------------------------- */
+
+/* Error flag at byte i of a string whose bytes start at position st of the
+ * stage (bytes before st and from en on read as zero; i may equal en, the
+ * string's end position). */
+__device__ __forceinline__ bool flag_at(const uint8_t *stage, long long i, long long st, long long en)
+{
+    uint32_t p = 0, w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const long long a = i - 7 + k, b = i - 3 + k;
+        p |= (a >= st && a < en ? (uint32_t)stage[a] : 0u) << (8 * k);
+        w |= (b >= st && b < en ? (uint32_t)stage[b] : 0u) << (8 * k);
+    }
+    return (gputf_utf8_errors(p, w) >> 24) != 0;
+}
+
+__device__ __forceinline__ uint32_t len16_of(uint32_t b) { return ((b & 0xC0) != 0x80) + (b >= 0xF0); }
+
+/* Scalar finish of string s, by one thread: exact error start and class from
+ * the first flagged byte, or the first character that does not fit. */
+__device__ void finish_string8(const BatchDir &d, uint64_t s, uint64_t flag, uint64_t total)
+{
+    const uint8_t *in = static_cast<const uint8_t *>(d.in) + d.in_off[s];
+    const uint64_t n = d.in_off[s + 1] - d.in_off[s];
+    const uint64_t cap = d.out_off[s + 1] - d.out_off[s];
+    uint64_t err_pos = NONE;
+    int cls = GPUTF_E_OK;
+    if (flag != NONE && gputf_utf8_fixup(in, n, flag, &cls, &err_pos) != 0) cls = GPUTF_E_INTERNAL;
+    int32_t error = GPUTF_E_OK;
+    uint64_t pos = n, written = total;
+    uint64_t g = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (i == err_pos) {
+            error = cls;
+            pos = i;
+            written = g;
+            break;
+        }
+        const uint32_t b = in[i];
+        const uint32_t l = len16_of(b);
+        if ((b & 0xC0) != 0x80 && g + l > cap) {
+            error = GPUTF_E_OUTPUT_TOO_SMALL;
+            pos = i;
+            written = g;
+            break;
+        }
+        g += l;
+    }
+    if (error == GPUTF_E_OK && err_pos != NONE) {   /* the error sits at the end position */
+        error = cls;
+        pos = err_pos;
+        written = g;
+    }
+    d.res[s].error = error;
+    d.res[s].reserved = 0;
+    d.res[s].position = pos;
+    d.res[s].written = written;
+}
+
+template <int THREADS, int BPT>
+__device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHeader *hdr, BatchShared &sm,
+                            uint8_t *stage)
+{
+    constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    constexpr int HALO = 16;
+    const uint8_t *in = static_cast<const uint8_t *>(d.in);
+    uint16_t *out = static_cast<uint16_t *>(d.out);
+    const int tid = threadIdx.x;
+    const uint64_t x0 = t * TILE;
+    const uint64_t x1 = x0 + TILE < d.units ? x0 + TILE : d.units;
+
+    if (tid < 32) find_strings(d, sm, x0, t + 1 == d.tiles ? ~0ull : x1);
+    for (int i = tid; i < (int)TILE + 2 * HALO; i += THREADS) {
+        const long long x = (long long)x0 + i - HALO;
+        stage[i] = (x >= 0 && (uint64_t)x < d.units) ? in[x] : 0;
+    }
+    __syncthreads();
+
+    const uint64_t c0 = x0 + (uint64_t)tid * BPT;
+    const uint64_t c1 = c0 + BPT < x1 ? c0 + BPT : (x1 > c0 ? x1 : c0);
+    uint64_t s;
+    {
+        uint64_t lo = 0, hi = sm.n_cached;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (sm.off[mid] <= c0) lo = mid;
+            else hi = mid;
+        }
+        s = sm.s_first + lo;
+    }
+#define SIDX(x) ((long long)((x) - x0) + HALO)
+    /* phase A: units per byte, starts, first flagged byte per string */
+    bool f = false;
+    uint64_t v = 0;
+    if (c0 < c1) {
+        uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        uint64_t flagged = NONE;
+        for (uint64_t i = c0; i < c1; i++) {
+            while (i >= en) {
+                ss++;
+                st = en;
+                en = off_at(d, sm, ss + 1);
+            }
+            if (i == st) {
+                f = true;
+                v = 0;
+            }
+            const uint32_t b = stage[SIDX(i)];
+            v += len16_of(b);
+            /* the flag sees the string's own bytes before i (the halo holds
+             * the 7 before the tile) and zeros before the string's start */
+            if (flagged != ss && flag_at(stage, SIDX(i), SIDX(st), SIDX(en))) {
+                record_string_error(d.errw, ss, epoch, i - st);
+                flagged = ss;
+            }
+            if (i + 1 == en && flagged != ss && flag_at(stage, SIDX(en), SIDX(st), SIDX(en))) {   /* cut short at its end */
+                record_string_error(d.errw, ss, epoch, en - st);
+                flagged = ss;
+            }
+        }
+    }
+    bool ef, tf;
+    uint64_t ev, tv;
+    block_seg_scan<THREADS>(f, v, sm, &ef, &ev, &tf, &tv);
+    if (tid == 0) {
+        __threadfence();
+        st_release(d.status + t, seg_status(epoch, t == 0 ? ST_PREFIX : ST_AGGREGATE, tf, tv));
+    }
+    uint64_t carry = 0;
+    if (t > 0) carry = block_seg_look_back<THREADS>(d.status, (long long)t, epoch, &hdr->flags, sm);
+    if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
+    __threadfence();
+
+    /* phase B: units out at each lead, results of strings ending here */
+    if (c0 < c1) {
+        uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        uint64_t g = ef ? ev : carry + ev;
+        uint64_t ob = d.out_off[ss], oc = d.out_off[ss + 1] - ob;
+        for (uint64_t i = c0; i < c1; i++) {
+            while (i >= en) {
+                ss++;
+                st = en;
+                en = off_at(d, sm, ss + 1);
+                ob = d.out_off[ss];
+                oc = d.out_off[ss + 1] - ob;
+            }
+            if (i == st) g = 0;
+            const uint32_t b = stage[SIDX(i)];
+            if ((b & 0xC0) != 0x80) {
+                uint32_t q = b;
+#pragma unroll
+                for (int k = 1; k < 4; k++)
+                    q |= (i + k < en ? (uint32_t)stage[SIDX(i + k)] : 0u) << (8 * k);
+                const uint32_t b0 = q & 0xFF;
+                const uint32_t two = ((b0 & 0x1F) << 6) | ((q >> 8) & 0x3F);
+                const uint32_t three = ((b0 & 0x0F) << 12) | ((q >> 2) & 0x0FC0) | ((q >> 16) & 0x3F);
+                const uint32_t four = ((b0 & 0x07) << 18) | ((q << 4) & 0x3F000) | ((q >> 10) & 0x0FC0) |
+                                      ((q >> 24) & 0x3F);
+                const uint32_t x = four - 0x10000;
+                const uint32_t l = len16_of(b);
+                if (g + l <= oc) {
+                    if (l == 2) {
+                        out[ob + g] = (uint16_t)(0xD800 | ((x >> 10) & 0x3FF));
+                        out[ob + g + 1] = (uint16_t)(0xDC00 | (x & 0x3FF));
+                    } else {
+                        out[ob + g] = (uint16_t)(b0 < 0x80 ? b0 : (b0 < 0xE0 ? two : three));
+                    }
+                }
+                g += l;
+            }
+            if (i + 1 == en) {
+                const uint64_t e = string_error(d.errw, ss, epoch);
+                if (e == NONE && g <= oc) {
+                    d.res[ss].error = GPUTF_E_OK;
+                    d.res[ss].reserved = 0;
+                    d.res[ss].position = en - st;
+                    d.res[ss].written = g;
+                } else {
+                    finish_string8(d, ss, e, g);
+                }
+            }
+        }
+    }
+#undef SIDX
+    __syncthreads();
+}
+
+/* ------------------------------------------------------------------------
+ * The batched kernel: tickets [0, d8.tiles) are UTF-8 tiles, the rest
+ * UTF-16 tiles.  One tile per CTA, taken in ticket order.
+ * ---------------------------------------------------------------------- */
+template <int THREADS, int UPT8, int UPT16>
+__global__ void __launch_bounds__(THREADS)
+batch_kernel(BatchDir d8, BatchDir d16, WsHeader *hdr, unsigned long long *ws_words, uint64_t ws_nwords)
+{
+    constexpr uint64_t TILE8 = (uint64_t)THREADS * UPT8, TILE16 = (uint64_t)THREADS * UPT16;
+    __shared__ BatchShared sm;
+    __shared__ unsigned s_tile_flag;
+    __shared__ unsigned long long s_ticket;
+    extern __shared__ uint4 smem4[];
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&hdr->ticket, 1ull);
+    __syncthreads();
+    const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
+    const uint64_t t = s_ticket;
+    if (t < d8.tiles)
+        batch8_tile<THREADS, UPT8>(d8, t, epoch, hdr, sm, reinterpret_cast<uint8_t *>(smem4));
+    else if (t - d8.tiles < d16.tiles)
+        batch16_tile<THREADS, UPT16>(d16, t - d8.tiles, epoch, hdr, sm, reinterpret_cast<uint16_t *>(smem4));
+    (void)TILE8;
+    (void)TILE16;
+    if (!finish_cta(hdr, &s_tile_flag)) return;
+    reset_workspace(hdr, ws_words, ws_nwords);
+}
+
+/* ------------------------------------------------------------------------
+ * Launch: configurations chosen by the autotuner, by index.
+ * ---------------------------------------------------------------------- */
+template <int T, int U8, int U16>
+static cudaError_t launch_cfg(const BatchDir &a8, const BatchDir &a16, void *ws, uint64_t ws_nwords,
+                              cudaStream_t stream)
+{
+    BatchDir d8 = a8, d16 = a16;
+    d8.tiles = (d8.units + (uint64_t)T * U8 - 1) / ((uint64_t)T * U8);
+    d16.tiles = (d16.units + (uint64_t)T * U16 - 1) / ((uint64_t)T * U16);
+    if (d8.count && !d8.tiles) d8.tiles = 1;     /* a batch of empty strings still needs a tile */
+    if (d16.count && !d16.tiles) d16.tiles = 1;
+    auto *words = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
+    d8.status = words;
+    d16.status = d8.status + d8.tiles;
+    d8.errw = d16.status + d16.tiles;
+    d16.errw = d8.errw + d8.count;
+    const uint64_t grid = d8.tiles + d16.tiles;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = ((uint64_t)T * U16 + 16) * 2 > (uint64_t)T * U8 + 32 ? ((uint64_t)T * U16 + 16) * 2
+                                                                             : (uint64_t)T * U8 + 32;
+    batch_kernel<T, U8, U16><<<(unsigned)grid, T, smem, stream>>>(d8, d16, static_cast<WsHeader *>(ws), words,
+                                                                   ws_nwords);
+    return cudaGetLastError();
+}
+
+int batch_config_count() { return 4; }
+
+uint64_t batch_min_tile_units() { return 128 * 8; }
+
+cudaError_t launch_batch(int cfg, const BatchDir &d8, const BatchDir &d16, void *ws, uint64_t ws_nwords,
+                         cudaStream_t stream)
+{
+    switch (cfg) {
+    case 0: return launch_cfg<256, 16, 16>(d8, d16, ws, ws_nwords, stream);
+    case 1: return launch_cfg<256, 8, 8>(d8, d16, ws, ws_nwords, stream);
+    case 2: return launch_cfg<128, 16, 16>(d8, d16, ws, ws_nwords, stream);
+    case 3: return launch_cfg<128, 8, 8>(d8, d16, ws, ws_nwords, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gputf

@@ -50,8 +50,10 @@ static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
 constexpr unsigned FLAG_TIMEOUT = 1u;
 constexpr size_t HEADER_BYTES = 256;
 
-/* Tile status word: epoch (22 bits) | flag (2 bits) | value (40 bits). */
-constexpr unsigned EPOCH_BITS = 22;
+/* Tile status word: epoch (22 bits) | flag (2 bits) | value (40 bits).
+ * Epochs stay below 2^21 so that the batched kernel's status words (which
+ * spend one epoch bit on a flag) and per-string words never alias. */
+constexpr unsigned EPOCH_BITS = 21;
 constexpr unsigned EPOCH_LIMIT = 1u << EPOCH_BITS;
 constexpr uint64_t VALUE_MASK = (1ull << 40) - 1;
 constexpr uint64_t ST_AGGREGATE = 1;   /* value = this tile's own total            */

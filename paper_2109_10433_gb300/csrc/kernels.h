@@ -34,6 +34,24 @@ cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *
                                           unsigned long long *len, int sms, cudaStream_t s);
 cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s);
 
+/* Batched transcoding (batch.cu). */
+struct BatchDir {
+    uint64_t count;               /* strings */
+    uint64_t units;               /* input code units */
+    const void *in;
+    const uint64_t *in_off;
+    void *out;
+    const uint64_t *out_off;
+    DevResult *res;
+    uint64_t tiles;               /* filled in by launch_batch */
+    unsigned long long *status;   /* filled in by launch_batch */
+    unsigned long long *errw;     /* filled in by launch_batch */
+};
+int batch_config_count();
+uint64_t batch_min_tile_units();
+cudaError_t launch_batch(int cfg, const BatchDir &d8, const BatchDir &d16, void *ws, uint64_t ws_nwords,
+                         cudaStream_t s);
+
 }  // namespace gputf
 
 #endif

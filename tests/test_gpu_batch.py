@@ -1,0 +1,110 @@
+"""GPU parity of the batched C-ABI call: every string's result and output in a
+batch are those of the oracle on that string alone, for every tile
+configuration, with strings of all lengths (empty, one unit, spanning many
+tiles), errors at string edges, capacities that cut outputs short, and tiles
+holding more strings than the kernel caches."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_10433_gb300 as g
+    g.build()
+    return g
+
+
+def check(g, strings8, strings16, caps8=None, caps16=None, config=0):
+    from paper_2109_10433_gb300 import batch as B
+    b8 = B.DeviceBatch(strings8, B.UTF8_TO_UTF16, caps8) if strings8 is not None else None
+    b16 = B.DeviceBatch(strings16, B.UTF16_TO_UTF8, caps16) if strings16 is not None else None
+    ws = B.workspace_for(b8, b16)
+    B.batch_transcode(b8, b16, ws, config=config)
+    torch.cuda.synchronize()
+    for b, strings, fn in ((b8, strings8, oracle.utf8_to_utf16), (b16, strings16, oracle.utf16_to_utf8)):
+        if b is None:
+            continue
+        res = b.read_results()
+        caps = np.diff(b.out_offsets_host)
+        for s, data in enumerate(strings):
+            ref, ref_out = fn(data, cap=int(caps[s]))
+            assert tuple(res[s]) == tuple(ref), (s, len(data), res[s], ref, config)
+            assert np.array_equal(b.output(s, ref.written), ref_out), s
+    return b8, b16
+
+
+def test_workload_batch_every_config(g):
+    from paper_2109_10433_gb300 import batch as B
+    bt = W.string_batch(3, 1500)
+    s8 = [s for s, d in zip(bt.strings, bt.directions) if d == 0]
+    s16 = [s for s, d in zip(bt.strings, bt.directions) if d == 1]
+    assert bt.invalid.sum() > 5
+    for cfg in range(B.config_count()):
+        check(g, s8, s16, config=cfg)
+
+
+def test_empty_tiny_and_long_strings(g):
+    rng = np.random.default_rng(1)
+    s8, s16 = [], []
+    for i in range(400):
+        k = int(rng.integers(0, 6))
+        n = [0, 1, 2, 3, 5000, 70000][k]
+        s8.append(W.utf8_text(i, n, W.SCRIPT_MIXED))
+        s16.append(W.utf16_text(i, n, W.MIX_CJK_EMOJI))
+    check(g, s8, s16)
+    check(g, [np.zeros(0, np.uint8)] * 50, [np.zeros(0, np.uint16)] * 7)
+    check(g, [W.utf8_text(9, 300000, W.MIX_FOUR_BYTE_HEAVY)], None)
+
+
+def test_more_strings_in_a_tile_than_the_cache(g):
+    rng = np.random.default_rng(2)
+    s8 = [W.utf8_text(i, int(rng.integers(0, 4)), W.SCRIPT_MIXED) for i in range(6000)]
+    s16 = [W.utf16_text(i, int(rng.integers(0, 3)), W.MIX_CJK_EMOJI) for i in range(6000)]
+    for cfg in (0, 3):
+        check(g, s8, s16, config=cfg)
+
+
+def test_errors_at_string_edges(g):
+    rng = W.rng_for(5)
+    s8, s16 = [], []
+    for i in range(600):
+        base = W.utf8_text(i, int(rng.integers(1, 200)), W.MIX_FOUR_BYTE_HEAVY)
+        tok, _ = W.utf8_error_token(rng, W.UTF8_TOKEN_KINDS[i % 5])
+        tok = np.frombuffer(tok, np.uint8)
+        s8.append(np.concatenate([tok, base]) if i % 3 == 0 else
+                  np.concatenate([base, tok]) if i % 3 == 1 else base[:-1] if base.size > 1 else base)
+        b16 = W.utf16_text(i, int(rng.integers(1, 100)), W.MIX_CJK_EMOJI)
+        t16, _ = W.utf16_error_token(rng)
+        t16 = np.array(t16, np.uint16)
+        s16.append(np.concatenate([t16, b16]) if i % 3 == 0 else
+                   np.concatenate([b16, t16]) if i % 3 == 1 else b16)
+    # strings that end with a high surrogate and strings that start with a low one, back to back
+    s16 += [np.array([0x41, 0xD83D], np.uint16), np.array([0xDE00, 0x42], np.uint16)]
+    check(g, s8, s16)
+
+
+def test_capacities_cut_outputs(g):
+    rng = np.random.default_rng(4)
+    s8 = [W.utf8_text(i, int(rng.integers(1, 3000)), W.SCRIPT_MIXED) for i in range(300)]
+    s16 = [W.utf16_text(i, int(rng.integers(1, 3000)), W.MIX_CJK_EMOJI) for i in range(300)]
+    c8 = [int(rng.integers(0, oracle.utf16_length_from_utf8(s) + 2)) for s in s8]
+    c16 = [int(rng.integers(0, oracle.utf8_length_from_utf16(s) + 2)) for s in s16]
+    check(g, s8, s16, c8, c16)
+
+
+def test_batch_equals_single_string_calls(g):
+    strings = [W.utf16_text(i, 10000 + 37 * i, W.MIX_CJK_EMOJI) for i in range(5)]
+    _, b16 = check(g, None, strings)
+    res = b16.read_results()
+    for s, data in enumerate(strings):
+        r, out = g.utf16_to_utf8(torch.from_numpy(data.view(np.int16)).cuda())
+        assert tuple(r) == tuple(res[s])
+        assert np.array_equal(out[:r.written].cpu().numpy(), b16.output(s, r.written))

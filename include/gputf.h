@@ -194,6 +194,22 @@ int gputf_batch_config_count(void);
 gputf_status gputf_batch_transcode(const gputf_batch *utf8_to_utf16, const gputf_batch *utf16_to_utf8,
                                    int config, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* A batched launch recorded into a CUDA graph, for replay. */
+typedef struct gputf_graph gputf_graph;
+
+/* Records gputf_batch_transcode(...) on `stream` (which must not be the
+ * legacy default stream, nor already capturing) into a graph and
+ * instantiates it; *graph receives the handle.  Replays transcode the same
+ * device buffers again, with whatever they hold at replay time.  Creating the
+ * graph allocates host-side graph objects; replaying does not. */
+gputf_status gputf_batch_graph_create(const gputf_batch *utf8_to_utf16, const gputf_batch *utf16_to_utf8,
+                                      int config, void *ws, size_t ws_bytes, cudaStream_t stream,
+                                      gputf_graph **graph);
+/* Enqueues one replay of the graph on `stream`. */
+gputf_status gputf_graph_launch(gputf_graph *graph, cudaStream_t stream);
+/* Releases the graph. */
+void gputf_graph_destroy(gputf_graph *graph);
+
 /* Largest input, in 16-bit units, that gputf_utf16_to_utf8_static accepts
  * (32 Mi units, 64 MiB of UTF-16). */
 #define GPUTF_STATIC_MAX_UNITS (((uint64_t)1) << 25)

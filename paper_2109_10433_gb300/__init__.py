@@ -56,6 +56,9 @@ SIGNATURES = {
     "gputf_batch_workspace_bytes": ([ctypes.c_uint64] * 4, _S),
     "gputf_batch_config_count": ([], _I),
     "gputf_batch_transcode": ([_P, _P, _I, _P, _S, _P], _I),
+    "gputf_batch_graph_create": ([_P, _P, _I, _P, _S, _P, _P], _I),
+    "gputf_graph_launch": ([_P, _P], _I),
+    "gputf_graph_destroy": ([_P], None),
     "gputf_error_name": ([ctypes.c_int32], ctypes.c_char_p),
     "gputf_status_name": ([_I], ctypes.c_char_p),
     "gputf_last_cuda_error": ([], _I),

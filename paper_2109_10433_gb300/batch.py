@@ -88,5 +88,38 @@ def batch_transcode(b8: DeviceBatch | None, b16: DeviceBatch | None, ws: Workspa
            "gputf_batch_transcode")
 
 
-__all__ = ["DeviceBatch", "batch_transcode", "workspace_for", "config_count", "UTF8_TO_UTF16",
+class BatchGraph:
+    """A batched launch captured into a CUDA graph (gputf_batch_graph_create)
+    on a stream of its own; replay() enqueues it on that stream."""
+
+    def __init__(self, b8: DeviceBatch | None, b16: DeviceBatch | None, ws: Workspace, config: int = 0):
+        import torch
+        self.stream = torch.cuda.Stream()
+        self._keep = (b8, b16, ws)
+        self._c8 = b8.cstruct() if b8 is not None else None
+        self._c16 = b16.cstruct() if b16 is not None else None
+        self.handle = ctypes.c_void_p()
+        torch.cuda.synchronize()
+        _check(lib().gputf_batch_graph_create(
+            ctypes.byref(self._c8) if self._c8 is not None else None,
+            ctypes.byref(self._c16) if self._c16 is not None else None,
+            int(config), ws.ptr, ws.nbytes, _stream(self.stream), ctypes.byref(self.handle)),
+            "gputf_batch_graph_create")
+
+    def replay(self):
+        _check(lib().gputf_graph_launch(self.handle, _stream(self.stream)), "gputf_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().gputf_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["BatchGraph", "DeviceBatch", "batch_transcode", "workspace_for", "config_count", "UTF8_TO_UTF16",
            "UTF16_TO_UTF8", "GputfError"]

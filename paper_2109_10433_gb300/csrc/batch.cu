@@ -35,19 +35,19 @@ __device__ __forceinline__ uint64_t seg_status(unsigned epoch, uint64_t flag, bo
            (value & VALUE_MASK);
 }
 
-/* Per-string error words: (epoch << 40) | (VALUE_MASK - position), combined
+/* Per-string error words: (epoch << 43) | (VALUE_MASK - position), combined
  * with atomicMax, so the smallest position of the current call wins and
  * words from earlier calls (smaller epochs) never read as current. */
 __device__ __forceinline__ void record_string_error(unsigned long long *errw, uint64_t s, unsigned epoch,
                                                     uint64_t pos)
 {
-    atomicMax(errw + s, ((unsigned long long)epoch << 40) | (VALUE_MASK - pos));
+    atomicMax(errw + s, ((unsigned long long)epoch << 43) | (VALUE_MASK - pos));
 }
 
 __device__ __forceinline__ uint64_t string_error(const unsigned long long *errw, uint64_t s, unsigned epoch)
 {
     const uint64_t w = ld_relaxed(errw + s);
-    return (unsigned)(w >> 40) == epoch ? VALUE_MASK - (w & VALUE_MASK) : NONE;
+    return (unsigned)(w >> 43) == epoch ? VALUE_MASK - (w & VALUE_MASK) : NONE;
 }
 
 constexpr int BATCH_OFF_CACHE = 512;   /* string offsets cached per tile */

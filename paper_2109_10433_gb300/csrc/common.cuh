@@ -50,9 +50,12 @@ static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
 constexpr unsigned FLAG_TIMEOUT = 1u;
 constexpr size_t HEADER_BYTES = 256;
 
-/* Tile status word: epoch (22 bits) | flag (2 bits) | value (40 bits).
- * Epochs stay below 2^21 so that the batched kernel's status words (which
- * spend one epoch bit on a flag) and per-string words never alias. */
+/* Epoch-tagged words (tile status words of every kernel, and the batched
+ * kernel's per-string error words) all keep the epoch of the call that wrote
+ * them in bits 43..63.  A word left by an earlier call, whatever kind of word
+ * it was, then carries a smaller epoch and never reads as current, even when
+ * a later call lays the workspace out differently.
+ * Tile status word: epoch (21 bits) | spare (1) | flag (2) | value (40). */
 constexpr unsigned EPOCH_BITS = 21;
 constexpr unsigned EPOCH_LIMIT = 1u << EPOCH_BITS;
 constexpr uint64_t VALUE_MASK = (1ull << 40) - 1;
@@ -61,7 +64,7 @@ constexpr uint64_t ST_PREFIX = 2;      /* value = total of this tile and all bef
 
 __device__ __forceinline__ uint64_t make_status(unsigned epoch, uint64_t flag, uint64_t value)
 {
-    return ((uint64_t)epoch << 42) | (flag << 40) | (value & VALUE_MASK);
+    return ((uint64_t)epoch << 43) | (flag << 40) | (value & VALUE_MASK);
 }
 
 __device__ __forceinline__ void st_release(unsigned long long *p, uint64_t v)
@@ -106,7 +109,7 @@ __device__ __forceinline__ uint64_t look_back(unsigned long long *status, long l
             unsigned ns = 32;
             while (true) {
                 uint64_t w = ld_acquire(status + idx);
-                if ((unsigned)(w >> 42) == epoch && ((w >> 40) & 3) != 0) {
+                if ((unsigned)(w >> 43) == epoch && ((w >> 40) & 3) != 0) {
                     flag = (w >> 40) & 3;
                     value = w & VALUE_MASK;
                     break;
@@ -160,7 +163,7 @@ __device__ __forceinline__ uint64_t block_look_back(unsigned long long *status, 
             unsigned ns = 32;
             while (true) {
                 const uint64_t w = ld_acquire(status + idx);
-                if ((unsigned)(w >> 42) == epoch && ((w >> 40) & 3) != 0) {
+                if ((unsigned)(w >> 43) == epoch && ((w >> 40) & 3) != 0) {
                     flag = (w >> 40) & 3;
                     value = w & VALUE_MASK;
                     break;

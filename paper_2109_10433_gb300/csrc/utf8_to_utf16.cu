@@ -314,7 +314,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             if (c_tile > 0) {
                 const bool in_window = lb_idx >= 0;
                 const uint64_t flag = in_window ? ((lb_word >> 40) & 3) : ST_PREFIX;
-                const bool ok = !in_window || ((unsigned)(lb_word >> 42) == epoch && flag != 0);
+                const bool ok = !in_window || ((unsigned)(lb_word >> 43) == epoch && flag != 0);
                 const unsigned pmask = __ballot_sync(FULL_MASK, ok && flag == ST_PREFIX);
                 const unsigned bad = __ballot_sync(FULL_MASK, !ok);
                 const int lane = tid & 31, wid = tid >> 5;

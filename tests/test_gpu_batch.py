@@ -108,3 +108,68 @@ def test_batch_equals_single_string_calls(g):
         r, out = g.utf16_to_utf8(torch.from_numpy(data.view(np.int16)).cuda())
         assert tuple(r) == tuple(res[s])
         assert np.array_equal(out[:r.written].cpu().numpy(), b16.output(s, r.written))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_full_size_workload_batch(g, graph):
+    """The 100,000-string workload at full size, in the launch the benchmark
+    times (autotuned configuration; graph replay), against the oracle."""
+    from paper_2109_10433_gb300 import batch as B
+    bt = W.string_batch(3, 100000)
+    s8 = [s for s, d in zip(bt.strings, bt.directions) if d == 0]
+    s16 = [s for s, d in zip(bt.strings, bt.directions) if d == 1]
+    b8 = B.DeviceBatch(s8, B.UTF8_TO_UTF16)
+    b16 = B.DeviceBatch(s16, B.UTF16_TO_UTF8)
+    ws = B.workspace_for(b8, b16)
+    if graph:
+        gr = B.BatchGraph(b8, b16, ws, 0)
+        for _ in range(3):
+            gr.replay()
+    else:
+        B.batch_transcode(b8, b16, ws, config=0)
+    torch.cuda.synchronize()
+    bad = []
+    for b, strings, fn in ((b8, s8, oracle.utf8_to_utf16), (b16, s16, oracle.utf16_to_utf8)):
+        res = b.read_results()
+        out = b.out.cpu().numpy()
+        if b.direction == B.UTF8_TO_UTF16:
+            out = out.view(np.uint16)
+        for s, data in enumerate(strings):
+            ref, ref_out = fn(data)
+            a = int(b.out_offsets_host[s])
+            if tuple(res[s]) != tuple(ref) or not np.array_equal(out[a:a + ref.written], ref_out):
+                bad.append((b.direction, s, len(data), tuple(res[s]), tuple(ref)))
+    assert not bad, (len(bad), bad[:5])
+
+
+def test_one_workspace_across_configurations_and_single_calls(g):
+    """One workspace used in turn by every tile configuration (which lay it out
+    differently) and by single-string calls: no call may read another's words."""
+    from paper_2109_10433_gb300 import batch as B
+    rng = W.rng_for(8)
+    s8, s16 = [], []
+    for i in range(800):
+        t = W.utf8_text(i, int(rng.integers(1, 400)), W.SCRIPT_MIXED)
+        if i % 7 == 0:
+            tok, _ = W.utf8_error_token(rng, W.UTF8_TOKEN_KINDS[i % 5])
+            t = np.concatenate([t, np.frombuffer(tok, np.uint8)])
+        s8.append(t)
+        u = W.utf16_text(i, int(rng.integers(1, 300)), W.MIX_CJK_EMOJI)
+        if i % 7 == 3:
+            u = np.concatenate([u, np.array([0xD800], np.uint16)])
+        s16.append(u)
+    b8 = B.DeviceBatch(s8, B.UTF8_TO_UTF16)
+    b16 = B.DeviceBatch(s16, B.UTF16_TO_UTF8)
+    ws = B.workspace_for(b8, b16)
+    expect8 = [oracle.utf8_to_utf16(s)[0] for s in s8]
+    expect16 = [oracle.utf16_to_utf8(s)[0] for s in s16]
+    for rnd in range(3):
+        for cfg in list(range(B.config_count())) + [0, 3, 1]:
+            B.batch_transcode(b8, b16, ws, config=cfg)
+            torch.cuda.synchronize()
+            assert [tuple(r) for r in b8.read_results()] == [tuple(r) for r in expect8], (rnd, cfg)
+            assert [tuple(r) for r in b16.read_results()] == [tuple(r) for r in expect16], (rnd, cfg)
+        # the same workspace for a single-buffer call in between
+        d = torch.from_numpy(s16[0].view(np.int16).copy()).cuda()
+        r, _ = g.utf16_to_utf8(d, ws=ws)
+        assert tuple(r) == tuple(expect16[0])

@@ -431,6 +431,116 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Served form: requests with Poisson arrivals, sizes log-uniform
+    64 B - 16 MiB of input, scripts and directions as in the batched form,
+    a fifth of them validate-only and 1% invalid, inputs resident on the
+    device before they arrive, an 8 GB admission budget over four batch
+    slots.  Reports the saturated throughput (every request waiting at
+    start) and p50/p99 latency at 50/80/95% of it, with every request's
+    result checked against its standalone call."""
+    import ctypes
+
+    import torch
+
+    import paper_2109_10433_gb300 as g
+    from paper_2109_10433_gb300 import serve as S
+
+    g.build()
+    torch.cuda.set_device(0)
+    t_gen = time.perf_counter()
+    w = W.serve_workload(4, args.requests)
+    gen_s = time.perf_counter() - t_gen
+    pool = S.DevicePool(list(w.texts) + list(w.payloads))
+    nt = len(w.texts)
+
+    def requests():
+        out = []
+        for i in range(w.units.size):
+            s = int(w.source[i])
+            k = s if s >= 0 else nt + (-1 - s)
+            ub = 1 + int(w.direction[i])
+            out.append(S.Request(i, int(w.direction[i]), S.VALIDATE if w.validate_only[i] else S.TRANSCODE,
+                                 pool.ptr(k, int(w.offset[i]) * ub), int(w.units[i])))
+        return out
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    srv = S.Server(budget_bytes=args.budget_gb << 30, slots=args.slots, max_requests=args.max_requests,
+                   big_units=args.big_units)
+    in_bytes = int(w.input_bytes().sum())
+    mean_bytes = in_bytes / w.units.size
+
+    def run(times, reqs):
+        srv.completed = []
+        l0 = srv.launches
+        b0 = srv.batches
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        t0 = S.run_arrivals(srv, reqs, times)
+        clk = clocks.stop()
+        t_end = max(r.done for r in reqs)
+        lat = S.latency_ms(reqs)
+        return {"requests": len(reqs), "seconds": t_end - t0, "achieved_gbs": in_bytes / (t_end - t0) / 1e9,
+                "batches": srv.batches - b0, "gpu_launches": srv.launches - l0, **lat, "clocks": clk}
+
+    # warm-up: a few hundred requests, all at once
+    warm = requests()[:min(400, w.units.size)]
+    S.run_arrivals(srv, warm, np.zeros(len(warm)))
+    torch.cuda.synchronize()
+
+    sat_reqs = requests()
+    sat = run(np.zeros(len(sat_reqs)), sat_reqs)
+    cap_gbs = sat["achieved_gbs"]
+    levels = []
+    for frac in (0.5, 0.8, 0.95):
+        offered = frac * cap_gbs
+        times = np.cumsum(w.gaps) * (mean_bytes / (offered * 1e9))
+        lv = run(times, requests())
+        lv["offered_frac"] = frac
+        lv["offered_gbs"] = offered
+        levels.append(lv)
+
+    # every result of the saturated run against the standalone call on the same input
+    L = g.lib()
+    ws1 = g.Workspace(16 << 20)
+    r1 = torch.zeros((len(sat_reqs), 3), dtype=torch.int64, device="cuda")
+    scratch = torch.empty(3 * (16 << 20) + 256, dtype=torch.uint8, device="cuda")
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for j, r in enumerate(sat_reqs):
+        rp, ip = ctypes.c_void_p(r1.data_ptr() + 24 * j), ctypes.c_void_p(r.ptr)
+        if r.op == S.TRANSCODE:
+            fn = L.gputf_utf8_to_utf16 if r.direction == 0 else L.gputf_utf16_to_utf8
+            st = fn(ip, r.units, ctypes.c_void_p(scratch.data_ptr()), r.out_units, ws1.ptr, ws1.nbytes, rp, sp)
+        else:
+            fn = L.gputf_validate_utf8 if r.direction == 0 else L.gputf_validate_utf16
+            st = fn(ip, r.units, ws1.ptr, ws1.nbytes, rp, sp)
+        if st != 0:
+            raise RuntimeError(f"standalone call status {st}")
+    got = r1.cpu().numpy()
+    same = all((int(got[j][0]) & 0xFFFFFFFF, int(got[j][1]), int(got[j][2])) == tuple(r.result)
+               for j, r in enumerate(sat_reqs))
+    invalid = sum(1 for r in sat_reqs if r.result.error != 0)
+    line = {
+        "metric": "served transcoding: sustained input GB/s with p50/p99 latency",
+        "value": cap_gbs, "unit": "GB/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": sat["seconds"] * 1e3, "higher_is_better": True, "dtype": "u8/u16", "data": "synthetic",
+        "config": {"workload": f"serve_{w.units.size}_requests_loguniform_64B_16MiB_poisson",
+                   "input_bytes": in_bytes, "budget_bytes": srv.budget_bytes, "device_bytes": srv.device_bytes,
+                   "slots": len(srv.slots), "max_requests_per_slot": srv.max_requests, "big_units": srv.big_units,
+                   "validate_only_requests": int(w.validate_only.sum()), "generation_s": gen_s},
+        "saturated": sat, "levels": levels,
+        "p50_ms": levels[1]["p50_ms"], "p99_ms": levels[1]["p99_ms"],
+        "invalid_requests": invalid, "results_identical_to_standalone": same,
+        "gpu_launches": sat["gpu_launches"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,12 +551,19 @@ def main():
     ap.add_argument("--e2e-warmup", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch"])
+    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--budget-gb", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--max-requests", type=int, default=4096)
+    ap.add_argument("--big-units", type=int, default=1 << 20)
     ap.add_argument("--strings", type=int, default=100000)
     ap.add_argument("--sample", type=int, default=2000)
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":
         return run_batch(args)
+    if args.workload == "serve" and args.impl != "reference":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

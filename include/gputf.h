@@ -164,6 +164,10 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
  *                    needed to size the launch;
  *   out, out_offsets : device; string s may write output code units
  *                    out[out_offsets[s] .. out_offsets[s+1]) (its capacity);
+ *                    out == NULL validates only: nothing is written, no
+ *                    capacity applies, out_offsets is ignored (may be NULL)
+ *                    and each result is what gputf_validate_utf8 /
+ *                    gputf_validate_utf16 gives the string (`written` 0);
  *   results        : device; count results, as gputf_result for a single
  *                    string, positions and `written` relative to the string. */
 typedef struct gputf_batch {
@@ -209,6 +213,105 @@ gputf_status gputf_batch_graph_create(const gputf_batch *utf8_to_utf16, const gp
 gputf_status gputf_graph_launch(gputf_graph *graph, cudaStream_t stream);
 /* Releases the graph. */
 void gputf_graph_destroy(gputf_graph *graph);
+
+/* One span of a gather: `bytes` bytes at device address `src`, copied to
+ * dst + dst_offset. */
+typedef struct gputf_span {
+    const void *src;
+    uint64_t dst_offset;
+    uint64_t bytes;
+} gputf_span;
+
+/* Copies `count` spans into the device buffer `dst` in one launch.  The
+ * paper has no counterpart: this assembles many requests' inputs, wherever
+ * they sit on the device, into the back-to-back layout that
+ * gputf_batch_transcode reads (the served form of the batched call).
+ *   spans : device array of `count` spans, 8-byte aligned; sources and
+ *           destinations may have any alignment; destination ranges must
+ *           not overlap each other or any source.  A block copies one span
+ *           at a time, so very long spans are best split by the caller.
+ * Enqueued on `stream`; allocates nothing.  INVALID_ARGUMENT for NULL
+ * pointers with count > 0. */
+gputf_status gputf_gather(const gputf_span *spans, uint64_t count, void *dst, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Served batches.  The paper has no counterpart: these calls turn a set of
+ * independent requests into the calls above (one gather, one batched
+ * transcode launch, one batched validate launch, one single-buffer call per
+ * large request), so that a request loop can hand the library a whole batch
+ * at once.  Every request gets the result (and output) of the single call on
+ * its input.
+ * ------------------------------------------------------------------------ */
+
+/* One request.  `in` is device memory holding `units` input code units (a
+ * UTF-16 input 2-byte aligned). */
+typedef struct gputf_request {
+    const void *in;
+    uint64_t units;
+    uint32_t direction;   /* 0: UTF-8 -> UTF-16LE, 1: UTF-16LE -> UTF-8        */
+    uint32_t op;          /* 0: transcode, 1: validate only                     */
+} gputf_request;
+
+/* Where a request of a planned batch goes. */
+typedef struct gputf_placement {
+    uint64_t row;          /* its result: results[row]                              */
+    uint64_t in_offset;    /* arena byte offset of its gathered input; UINT64_MAX
+                              when it runs in place (units >= big_units)             */
+    uint64_t out_offset;   /* arena byte offset of its output (capacity: n UTF-16
+                              units, or 3n UTF-8 bytes); UINT64_MAX when validating */
+} gputf_placement;
+
+/* The device and pinned host memory one batch slot owns, all caller-owned.
+ *   arena / arena_bytes : device, 256-byte aligned; inputs gathered back to
+ *                         back, then outputs;
+ *   meta / meta_host / meta_bytes : device and pinned host buffers of the same
+ *                         size (gputf_serve_meta_bytes), 8-byte aligned: gather
+ *                         spans and CSR offsets, written to meta_host and copied;
+ *   results / results_host : device and pinned host arrays of max_requests
+ *                         results; the results are copied back at the end;
+ *   ws, ws_bytes   : workspace of at least gputf_batch_workspace_bytes(
+ *                    arena_bytes, max_requests, arena_bytes / 2, max_requests);
+ *   ws1, ws1_bytes : workspace of at least gputf_workspace_bytes(u), u the
+ *                    largest request run in place.
+ * A slot serves one batch at a time: meta_host and results_host may be
+ * touched again only once the stream has passed the batch. */
+typedef struct gputf_slot {
+    void *arena;
+    uint64_t arena_bytes;
+    void *meta;
+    void *meta_host;
+    uint64_t meta_bytes;
+    gputf_result *results;
+    gputf_result *results_host;
+    uint64_t max_requests;
+    void *ws;
+    uint64_t ws_bytes;
+    void *ws1;
+    uint64_t ws1_bytes;
+} gputf_slot;
+
+/* Bytes of metadata a slot needs for up to max_requests requests whose
+ * gathered inputs fill at most arena_bytes. */
+size_t gputf_serve_meta_bytes(uint64_t max_requests, uint64_t arena_bytes);
+
+/* Plans a batch without touching the GPU: requests with units >= big_units
+ * run in place; the others are grouped by (direction, op) in the order
+ * given.  place[i] receives request i's placement; *arena_bytes and
+ * *meta_bytes the arena and metadata the batch needs.  INVALID_ARGUMENT for
+ * a bad direction or op, a NULL pointer, or a misaligned UTF-16 input. */
+gputf_status gputf_serve_plan(const gputf_request *reqs, uint64_t count, uint64_t big_units,
+                              gputf_placement *place, uint64_t *arena_bytes, uint64_t *meta_bytes);
+
+/* Plans (as above) and enqueues one batch on `stream`: the metadata copy,
+ * the gather of the small requests' inputs (gputf_gather), the batched
+ * transcode and validate launches (gputf_batch_transcode with `config`),
+ * one single-buffer call per large request, and the copy of the results to
+ * results_host.  WORKSPACE_TOO_SMALL when the batch needs more arena,
+ * metadata, result rows or workspace than the slot has; nothing is enqueued
+ * then.  Allocates nothing. */
+gputf_status gputf_serve_launch(const gputf_slot *slot, const gputf_request *reqs, uint64_t count,
+                                uint64_t big_units, int config, gputf_placement *place,
+                                cudaStream_t stream);
 
 /* Largest input, in 16-bit units, that gputf_utf16_to_utf8_static accepts
  * (32 Mi units, 64 MiB of UTF-16). */

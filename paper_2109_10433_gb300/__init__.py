@@ -59,6 +59,10 @@ SIGNATURES = {
     "gputf_batch_graph_create": ([_P, _P, _I, _P, _S, _P, _P], _I),
     "gputf_graph_launch": ([_P, _P], _I),
     "gputf_graph_destroy": ([_P], None),
+    "gputf_gather": ([_P, ctypes.c_uint64, _P, _P], _I),
+    "gputf_serve_meta_bytes": ([ctypes.c_uint64, ctypes.c_uint64], _S),
+    "gputf_serve_plan": ([_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P], _I),
+    "gputf_serve_launch": ([_P, _P, ctypes.c_uint64, ctypes.c_uint64, _I, _P, _P], _I),
     "gputf_error_name": ([ctypes.c_int32], ctypes.c_char_p),
     "gputf_status_name": ([_I], ctypes.c_char_p),
     "gputf_last_cuda_error": ([], _I),

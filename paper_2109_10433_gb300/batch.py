@@ -34,9 +34,10 @@ def default_capacity(direction: int, n_units: np.ndarray) -> np.ndarray:
 class DeviceBatch:
     """One direction of a batch, resident on the device."""
 
-    def __init__(self, strings, direction: int, capacities=None, device="cuda"):
+    def __init__(self, strings, direction: int, capacities=None, device="cuda", validate_only: bool = False):
         import torch
         self.direction = direction
+        self.validate_only = validate_only
         dtype = np.uint8 if direction == UTF8_TO_UTF16 else np.uint16
         sizes = np.array([len(s) for s in strings], dtype=np.int64)
         self.count = len(strings)
@@ -56,8 +57,11 @@ class DeviceBatch:
         self.results = torch.zeros((max(self.count, 1), 3), dtype=torch.int64, device=device)
 
     def cstruct(self) -> CBatch:
+        """The C descriptor; validate-only batches pass no output (out = NULL)."""
+        out = None if self.validate_only else _ptr(self.out).value
+        out_off = None if self.validate_only else _ptr(self.out_offsets).value
         return CBatch(self.count, self.units, _ptr(self.inp).value, _ptr(self.in_offsets).value,
-                      _ptr(self.out).value, _ptr(self.out_offsets).value, _ptr(self.results).value)
+                      out, out_off, _ptr(self.results).value)
 
     def read_results(self) -> list:
         v = self.results.cpu().numpy()[:self.count]

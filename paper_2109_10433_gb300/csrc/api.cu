@@ -82,6 +82,8 @@ __global__ void workspace_header_init(gputf::WsHeader *h)
 }  // namespace
 
 namespace gputf {
+gputf_status status_of(cudaError_t e) { return cuda_status(e); }
+
 cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(ws, 0, bytes, s);
@@ -248,7 +250,7 @@ gputf_status gputf_batch_transcode(const gputf_batch *b8, const gputf_batch *b16
     for (int k = 0; k < 2; k++) {
         if (b[k] == nullptr || b[k]->count == 0) continue;
         const gputf_batch &x = *b[k];
-        if (x.in_offsets == nullptr || x.out_offsets == nullptr || x.results == nullptr ||
+        if (x.in_offsets == nullptr || (x.out != nullptr && x.out_offsets == nullptr) || x.results == nullptr ||
             (x.units > 0 && x.in == nullptr) || !aligned(x.results, 8) || !aligned(x.in_offsets, 8) ||
             !aligned(x.out_offsets, 8) || (k == 1 && !aligned(x.in, 2)) || (k == 0 && !aligned(x.out, 2)))
             return GPUTF_STATUS_INVALID_ARGUMENT;
@@ -258,7 +260,7 @@ gputf_status gputf_batch_transcode(const gputf_batch *b8, const gputf_batch *b16
         d[k].in = x.in;
         d[k].in_off = x.in_offsets;
         d[k].out = x.out;
-        d[k].out_off = x.out_offsets;
+        d[k].out_off = x.out != nullptr ? x.out_offsets : nullptr;
         d[k].res = reinterpret_cast<gputf::DevResult *>(x.results);
     }
     if (config < 0) config = 0;
@@ -270,6 +272,16 @@ gputf_status gputf_batch_transcode(const gputf_batch *b8, const gputf_batch *b16
     gputf_status st = current_device(&sms);
     if (st != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_batch(config, d[0], d[1], ws, (ws_bytes - gputf::HEADER_BYTES) / 8, stream));
+}
+
+gputf_status gputf_gather(const gputf_span *spans, uint64_t count, void *dst, cudaStream_t stream)
+{
+    if (count == 0) return GPUTF_STATUS_OK;
+    if (spans == nullptr || dst == nullptr || !aligned(spans, 8)) return GPUTF_STATUS_INVALID_ARGUMENT;
+    int sms;
+    gputf_status st = current_device(&sms);
+    if (st != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_gather(spans, count, dst, sms, stream));
 }
 
 const char *gputf_error_name(int32_t error)

@@ -70,6 +70,67 @@ __device__ __forceinline__ uint64_t off_at(const BatchDir &d, const BatchShared 
     return j < sm.n_cached ? sm.off[j] : d.in_off[s];
 }
 
+/* Output units of a string before absolute position x (st <= x <= en):
+ * the published status words of the string's whole tiles before x's tile,
+ * walked back like the look-back (to a PREFIX word or the string's first
+ * tile), plus len(j) summed over the units of x's own tile before x.  The
+ * words are all published by the time the string's last tile runs its
+ * phase B.  Cost: the string's tile count plus one tile, not its length.
+ * Returns false if a word is not published (a broken invariant). */
+template <uint64_t TILE, typename LenFn>
+__device__ bool string_prefix(const BatchDir &d, unsigned epoch, uint64_t st, uint64_t x, LenFn len,
+                              uint64_t *out)
+{
+    const uint64_t xs = x / TILE * TILE;
+    uint64_t sum = 0;
+    for (uint64_t j = st > xs ? st : xs; j < x; j++) sum += len(j);
+    if (st < xs) {
+        for (long long k = (long long)(x / TILE) - 1; k >= 0; k--) {
+            const uint64_t w = ld_acquire(d.status + k);
+            const uint64_t fl = (w >> 40) & 3;
+            if ((unsigned)(w >> 43) != (epoch & SEG_EPOCH_MASK) || fl == 0) return false;
+            sum += w & VALUE_MASK;
+            if (fl == ST_PREFIX || ((w >> 42) & 1)) break;
+        }
+    }
+    *out = sum;
+    return true;
+}
+
+/* The first unit q of a string with len(q) > 0 whose output does not fit
+ * the capacity cap (g(q) <= cap < g(q) + len(q), g = output before q), with
+ * g(q): the tile holding it is found from the status words (output through
+ * each tile), then that tile is scanned.  Same cost bound as above.
+ * Returns false if there is no such unit or a word is not published. */
+template <uint64_t TILE, typename LenFn>
+__device__ bool string_crossing(const BatchDir &d, unsigned epoch, uint64_t st, uint64_t en, uint64_t cap,
+                                LenFn len, uint64_t *q, uint64_t *gq)
+{
+    const uint64_t t0 = st / TILE, t1 = (en - 1) / TILE;
+    uint64_t before = 0, k = t0;
+    for (; k < t1; k++) {
+        const uint64_t w = ld_acquire(d.status + k);
+        const uint64_t fl = (w >> 40) & 3;
+        if ((unsigned)(w >> 43) != (epoch & SEG_EPOCH_MASK) || fl == 0) return false;
+        const uint64_t v = w & VALUE_MASK;
+        const uint64_t through = (fl == ST_PREFIX || k == t0) ? v : before + v;
+        if (through > cap) break;
+        before = through;
+    }
+    uint64_t g = before;
+    const uint64_t a = st > k * TILE ? st : k * TILE, b = en < (k + 1) * TILE ? en : (k + 1) * TILE;
+    for (uint64_t j = a; j < b; j++) {
+        const uint64_t l = len(j);
+        if (l && g + l > cap) {
+            *q = j;
+            *gq = g;
+            return true;
+        }
+        g += l;
+    }
+    return false;
+}
+
 /* Warp 0: the last string s with in_off[s] <= x (the one containing unit x
  * when it is not empty), then the offsets from there to the first one at or
  * past x_end: the first BATCH_OFF_CACHE go into the cache, and every empty
@@ -292,40 +353,54 @@ __device__ __forceinline__ void put_bytes16(uint8_t *dst, uint32_t u, uint32_t n
     }
 }
 
-/* Scalar finish of string s (error and/or capacity), by one thread. */
-__device__ void finish_string16(const BatchDir &d, uint64_t s, uint64_t first_err, uint64_t total)
+/* Result of string s when it has an error or overflows its capacity, by
+ * one thread of the tile holding its last unit.  The error at unit p (the
+ * first unit flagged) wins unless output before it already overflows; then
+ * the result is OUTPUT_TOO_SMALL at the first unit that does not fit.
+ * `total` is the string's whole output.  Bounded work (string_prefix,
+ * string_crossing). */
+template <uint64_t TILE>
+__device__ void finish_string16(const BatchDir &d, unsigned epoch, uint64_t s, uint64_t first_err, uint64_t total)
 {
-    const uint16_t *in = static_cast<const uint16_t *>(d.in) + d.in_off[s];
-    const uint64_t n = d.in_off[s + 1] - d.in_off[s];
-    const uint64_t cap = d.out_off[s + 1] - d.out_off[s];
+    const uint16_t *in = static_cast<const uint16_t *>(d.in);
+    const uint64_t st = d.in_off[s], en = d.in_off[s + 1];
+    const uint64_t cap = d.out ? d.out_off[s + 1] - d.out_off[s] : ~0ull;   /* no limit when validating */
+    auto len = [&](uint64_t j) -> uint64_t {
+        const uint32_t prev = j > st ? in[j - 1] : 0u;
+        const uint32_t next = j + 1 < en ? in[j + 1] : 0u;
+        return bytes16(in[j], prev, next);
+    };
     int32_t error = GPUTF_E_OK;
-    uint64_t pos = n, written = total;
-    uint64_t g = 0;
-    /* walk characters up to the first error, stopping at the first one that
-     * does not fit */
-    for (uint64_t i = 0; i < n; i++) {
-        if (first_err != NONE && i == first_err) {
+    uint64_t pos = en - st, written = total;
+    bool ok = true;
+    bool crossing = first_err == NONE;
+    if (first_err != NONE) {
+        uint64_t gp = 0;
+        ok = string_prefix<TILE>(d, epoch, st, st + first_err, len, &gp);
+        if (gp <= cap) {
             error = GPUTF_E_SURROGATE;
-            pos = i;
-            written = g;
-            break;
+            pos = first_err;
+            written = gp;
+        } else {
+            crossing = true;
         }
-        const uint32_t u = in[i];
-        const uint32_t prev = i ? in[i - 1] : 0u;
-        const uint32_t next = i + 1 < n ? in[i + 1] : 0u;
-        const uint32_t l = bytes16(u, prev, next);
-        if (l && g + l > cap) {
-            error = GPUTF_E_OUTPUT_TOO_SMALL;
-            pos = i;
-            written = g;
-            break;
-        }
-        g += l;
+    }
+    if (ok && crossing && total > cap) {
+        uint64_t q = 0, gq = 0;
+        ok = string_crossing<TILE>(d, epoch, st, en, cap, len, &q, &gq);
+        error = GPUTF_E_OUTPUT_TOO_SMALL;
+        pos = q - st;
+        written = gq;
+    }
+    if (!ok) {
+        error = GPUTF_E_INTERNAL;
+        pos = 0;
+        written = 0;
     }
     d.res[s].error = error;
     d.res[s].reserved = 0;
     d.res[s].position = pos;
-    d.res[s].written = written;
+    d.res[s].written = d.out ? written : 0;
 }
 
 template <int THREADS, int UPT>
@@ -392,6 +467,10 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
         }
         (void)err_p;
     }
+    /* The look-back also orders the error words: a string's result is read
+     * only after every tile from its first on has published, so it runs
+     * when validating only (out == NULL) too. */
+    const bool wr = d.out != nullptr;
     bool ef, tf;
     uint64_t ev, tv;
     block_seg_scan<THREADS>(f, v, sm, &ef, &ev, &tf, &tv);
@@ -408,21 +487,21 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
     if (c0 < c1) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
         uint64_t g = ef ? ev : carry + ev;   /* output position within the string */
-        uint64_t ob = d.out_off[ss], oc = d.out_off[ss + 1] - ob;
+        uint64_t ob = wr ? d.out_off[ss] : 0, oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
         for (uint64_t i = c0; i < c1; i++) {
             while (i >= en) {
                 ss++;
                 st = en;
                 en = off_at(d, sm, ss + 1);
-                ob = d.out_off[ss];
-                oc = d.out_off[ss + 1] - ob;
+                ob = wr ? d.out_off[ss] : 0;
+                oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
             }
             if (i == st) g = 0;
             const uint32_t u = U16AT(i);
             const uint32_t prev = i > st ? U16AT(i - 1) : 0u;
             const uint32_t next = i + 1 < en ? U16AT(i + 1) : 0u;
             const uint32_t l = bytes16(u, prev, next);
-            if (l && g + l <= oc) put_bytes16(out + ob + g, u, next, l);
+            if (wr && l && g + l <= oc) put_bytes16(out + ob + g, u, next, l);
             g += l;
             if (i + 1 == en) {   /* the string's last unit: its result */
                 const uint64_t e = string_error(d.errw, ss, epoch);
@@ -430,9 +509,9 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
                     d.res[ss].error = GPUTF_E_OK;
                     d.res[ss].reserved = 0;
                     d.res[ss].position = en - st;
-                    d.res[ss].written = g;
+                    d.res[ss].written = wr ? g : 0;
                 } else {
-                    finish_string16(d, ss, e, g);
+                    finish_string16<TILE>(d, epoch, ss, e, g);
                 }
             }
         }
@@ -462,45 +541,54 @@ __device__ __forceinline__ bool flag_at(const uint8_t *stage, long long i, long 
 
 __device__ __forceinline__ uint32_t len16_of(uint32_t b) { return ((b & 0xC0) != 0x80) + (b >= 0xF0); }
 
-/* Scalar finish of string s, by one thread: exact error start and class from
- * the first flagged byte, or the first character that does not fit. */
-__device__ void finish_string8(const BatchDir &d, uint64_t s, uint64_t flag, uint64_t total)
+/* Result of string s when it has an error or overflows its capacity, by
+ * one thread of the tile holding its last unit: the exact error start p and
+ * class come from the first flagged byte (gputf_utf8_fixup, a few bytes of
+ * work); the error wins unless output before p already overflows, and then
+ * the result is OUTPUT_TOO_SMALL at the first lead that does not fit.
+ * Bounded work (string_prefix, string_crossing). */
+template <uint64_t TILE>
+__device__ void finish_string8(const BatchDir &d, unsigned epoch, uint64_t s, uint64_t flag, uint64_t total)
 {
-    const uint8_t *in = static_cast<const uint8_t *>(d.in) + d.in_off[s];
-    const uint64_t n = d.in_off[s + 1] - d.in_off[s];
-    const uint64_t cap = d.out_off[s + 1] - d.out_off[s];
-    uint64_t err_pos = NONE;
-    int cls = GPUTF_E_OK;
-    if (flag != NONE && gputf_utf8_fixup(in, n, flag, &cls, &err_pos) != 0) cls = GPUTF_E_INTERNAL;
+    const uint8_t *in = static_cast<const uint8_t *>(d.in);
+    const uint64_t st = d.in_off[s], en = d.in_off[s + 1];
+    const uint64_t n = en - st;
+    const uint64_t cap = d.out ? d.out_off[s + 1] - d.out_off[s] : ~0ull;   /* no limit when validating */
+    auto len = [&](uint64_t j) -> uint64_t { return len16_of(in[j]); };
     int32_t error = GPUTF_E_OK;
     uint64_t pos = n, written = total;
-    uint64_t g = 0;
-    for (uint64_t i = 0; i < n; i++) {
-        if (i == err_pos) {
+    bool ok = true;
+    bool crossing = flag == NONE;
+    if (flag != NONE) {
+        uint64_t err_pos = NONE;
+        int cls = GPUTF_E_OK;
+        ok = gputf_utf8_fixup(in + st, n, flag, &cls, &err_pos) == 0 && err_pos != NONE && err_pos <= n;
+        uint64_t gp = 0;
+        if (ok) ok = string_prefix<TILE>(d, epoch, st, st + err_pos, len, &gp);
+        if (ok && gp <= cap) {
             error = cls;
-            pos = i;
-            written = g;
-            break;
+            pos = err_pos;
+            written = gp;
+        } else {
+            crossing = true;
         }
-        const uint32_t b = in[i];
-        const uint32_t l = len16_of(b);
-        if ((b & 0xC0) != 0x80 && g + l > cap) {
-            error = GPUTF_E_OUTPUT_TOO_SMALL;
-            pos = i;
-            written = g;
-            break;
-        }
-        g += l;
     }
-    if (error == GPUTF_E_OK && err_pos != NONE) {   /* the error sits at the end position */
-        error = cls;
-        pos = err_pos;
-        written = g;
+    if (ok && crossing && total > cap) {
+        uint64_t q = 0, gq = 0;
+        ok = string_crossing<TILE>(d, epoch, st, en, cap, len, &q, &gq);
+        error = GPUTF_E_OUTPUT_TOO_SMALL;
+        pos = q - st;
+        written = gq;
+    }
+    if (!ok) {
+        error = GPUTF_E_INTERNAL;
+        pos = 0;
+        written = 0;
     }
     d.res[s].error = error;
     d.res[s].reserved = 0;
     d.res[s].position = pos;
-    d.res[s].written = written;
+    d.res[s].written = d.out ? written : 0;
 }
 
 template <int THREADS, int BPT>
@@ -565,6 +653,10 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
             }
         }
     }
+    /* The look-back also orders the error words: a string's result is read
+     * only after every tile from its first on has published, so it runs
+     * when validating only (out == NULL) too. */
+    const bool wr = d.out != nullptr;
     bool ef, tf;
     uint64_t ev, tv;
     block_seg_scan<THREADS>(f, v, sm, &ef, &ev, &tf, &tv);
@@ -581,18 +673,18 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
     if (c0 < c1) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
         uint64_t g = ef ? ev : carry + ev;
-        uint64_t ob = d.out_off[ss], oc = d.out_off[ss + 1] - ob;
+        uint64_t ob = wr ? d.out_off[ss] : 0, oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
         for (uint64_t i = c0; i < c1; i++) {
             while (i >= en) {
                 ss++;
                 st = en;
                 en = off_at(d, sm, ss + 1);
-                ob = d.out_off[ss];
-                oc = d.out_off[ss + 1] - ob;
+                ob = wr ? d.out_off[ss] : 0;
+                oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
             }
             if (i == st) g = 0;
             const uint32_t b = stage[SIDX(i)];
-            if ((b & 0xC0) != 0x80) {
+            if (wr && (b & 0xC0) != 0x80) {
                 uint32_t q = b;
 #pragma unroll
                 for (int k = 1; k < 4; k++)
@@ -620,9 +712,9 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                     d.res[ss].error = GPUTF_E_OK;
                     d.res[ss].reserved = 0;
                     d.res[ss].position = en - st;
-                    d.res[ss].written = g;
+                    d.res[ss].written = wr ? g : 0;
                 } else {
-                    finish_string8(d, ss, e, g);
+                    finish_string8<TILE>(d, epoch, ss, e, g);
                 }
             }
         }

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gputf.h"
+
 namespace gputf {
 
 /* Same layout as gputf_result in the public header. */
@@ -33,6 +35,12 @@ cudaError_t launch_utf16_length_from_utf8(const uint8_t *in, uint64_t n, void *w
 cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *ws,
                                           unsigned long long *len, int sms, cudaStream_t s);
 cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s);
+
+/* A CUDA error as a call status, recorded for gputf_last_cuda_error (api.cu). */
+gputf_status status_of(cudaError_t e);
+
+/* Span gather (gather.cu). */
+cudaError_t launch_gather(const gputf_span *spans, uint64_t count, void *dst, int sms, cudaStream_t s);
 
 /* Batched transcoding (batch.cu). */
 struct BatchDir {

@@ -100,6 +100,42 @@ def test_capacities_cut_outputs(g):
     check(g, s8, s16, c8, c16)
 
 
+def test_errors_and_capacity_deep_in_long_strings(g):
+    """Strings spanning many tiles with the first error, or the first unit
+    that does not fit, in any of their tiles (the result's `written` is then
+    found from the tiles' status words plus one tile), for every
+    configuration, transcoding and validating."""
+    from paper_2109_10433_gb300 import batch as B
+    rng = np.random.default_rng(9)
+    s8, s16, c8, c16 = [], [], [], []
+    for i in range(40):
+        n = int(rng.integers(20000, 90000))
+        t8 = W.utf8_error_text(100 + i, n, W.SCRIPT_MIXED, mean_gap=int(rng.integers(3000, 60000)))
+        t16 = W.utf16_text(200 + i, n // 2, W.MIX_CJK_EMOJI).copy()
+        k = int(rng.integers(0, t16.size))
+        if i % 3:
+            t16[k] = 0xD800 if i % 2 else 0xDC00      # a lone surrogate somewhere inside
+        s8.append(t8.data)
+        s16.append(t16)
+        l8 = oracle.utf16_length_from_utf8(t8.data)
+        l16 = oracle.utf8_length_from_utf16(t16)
+        # capacities: ample, or cut anywhere in the string
+        c8.append(int(rng.integers(0, l8 + 1)) if i % 4 == 0 else len(t8.data))
+        c16.append(int(rng.integers(0, l16 + 1)) if i % 4 == 1 else 3 * t16.size)
+    for cfg in range(B.config_count()):
+        check(g, s8, s16, c8, c16, config=cfg)
+    for cfg in (0, B.config_count() - 1):
+        b8 = B.DeviceBatch(s8, B.UTF8_TO_UTF16, validate_only=True)
+        b16 = B.DeviceBatch(s16, B.UTF16_TO_UTF8, validate_only=True)
+        ws = B.workspace_for(b8, b16)
+        B.batch_transcode(b8, b16, ws, config=cfg)
+        torch.cuda.synchronize()
+        for b, strings, val in ((b8, s8, oracle.validate_utf8), (b16, s16, oracle.validate_utf16)):
+            res = b.read_results()
+            for j, data in enumerate(strings):
+                assert tuple(res[j]) == tuple(val(data)), (cfg, j)
+
+
 def test_batch_equals_single_string_calls(g):
     strings = [W.utf16_text(i, 10000 + 37 * i, W.MIX_CJK_EMOJI) for i in range(5)]
     _, b16 = check(g, None, strings)
@@ -173,3 +209,30 @@ def test_one_workspace_across_configurations_and_single_calls(g):
         d = torch.from_numpy(s16[0].view(np.int16).copy()).cuda()
         r, _ = g.utf16_to_utf8(d, ws=ws)
         assert tuple(r) == tuple(expect16[0])
+
+
+def test_validate_only_batch_equals_single_validation(g):
+    """out == NULL validates only: each string's result is the oracle's
+    validation result (written 0), across tiles and configurations, with one
+    direction transcoding and the other validating in the same launch."""
+    from paper_2109_10433_gb300 import batch as B
+    bt = W.string_batch(11, 600)
+    s8 = [s for s, d in zip(bt.strings, bt.directions) if d == 0] + [np.zeros(0, np.uint8), W.utf8_text(5, 90000, W.SCRIPT_MIXED)]
+    s16 = [s for s, d in zip(bt.strings, bt.directions) if d == 1] + [np.zeros(0, np.uint16)]
+    for cfg in range(B.config_count()):
+        for v8, v16 in ((True, True), (True, False), (False, True)):
+            b8 = B.DeviceBatch(s8, B.UTF8_TO_UTF16, validate_only=v8)
+            b16 = B.DeviceBatch(s16, B.UTF16_TO_UTF8, validate_only=v16)
+            ws = B.workspace_for(b8, b16)
+            B.batch_transcode(b8, b16, ws, config=cfg)
+            torch.cuda.synchronize()
+            for b, strings, val, fn in ((b8, s8, oracle.validate_utf8, oracle.utf8_to_utf16),
+                                        (b16, s16, oracle.validate_utf16, oracle.utf16_to_utf8)):
+                res = b.read_results()
+                for s, data in enumerate(strings):
+                    if b.validate_only:
+                        assert tuple(res[s]) == tuple(val(data)), (cfg, s)
+                    else:
+                        ref, ref_out = fn(data)
+                        assert tuple(res[s]) == tuple(ref), (cfg, s)
+                        assert np.array_equal(b.output(s, ref.written), ref_out), (cfg, s)

@@ -315,3 +315,75 @@ def four_byte_heavy_utf8_64mib(seed: int = 2, nbytes: int = 64 * MiB,
     """64 MiB of UTF-8: 40% U+10000-10FFFF, 30% U+0800-FFFF (no surrogates),
     30% ASCII, with error tokens about once per MiB."""
     return utf8_error_text(seed, nbytes, MIX_FOUR_BYTE_HEAVY, mean_gap)
+
+
+# ---------------------------------------------------------------------------
+# Served requests: a stream of requests of log-uniform sizes, each a slice of
+# a pool text of its script and direction, cut at character boundaries.
+# ---------------------------------------------------------------------------
+@dataclass
+class ServeWorkload:
+    texts: list                 # index 2 * script + direction: uint8 (UTF-8) or uint16 (UTF-16) text
+    payloads: list              # private inputs of the invalid requests
+    direction: np.ndarray       # int8: 0 = UTF-8 -> UTF-16, 1 = UTF-16 -> UTF-8
+    validate_only: np.ndarray   # bool: validate without transcoding
+    invalid: np.ndarray         # bool: an error token was inserted
+    source: np.ndarray          # int64: text index, or -1 - k for payloads[k]
+    offset: np.ndarray          # int64: first unit within the text (0 for payloads)
+    units: np.ndarray           # int64: input code units
+    gaps: np.ndarray            # float64: inter-arrival gaps with mean 1 (exponential)
+
+    def input_bytes(self) -> np.ndarray:
+        return self.units * (1 + self.direction.astype(np.int64))
+
+
+def serve_workload(seed: int, n_requests: int, min_bytes: int = 64, max_bytes: int = 16 * MiB,
+                   validate_frac: float = 0.2, invalid_frac: float = 0.01,
+                   text_bytes: int = 24 * MiB) -> ServeWorkload:
+    """Requests with sizes log-uniform in [min_bytes, max_bytes] input bytes,
+    script uniform over SCRIPTS, a fair-coin direction, a fraction validated
+    only and a fraction carrying one error token, arriving with exponential
+    gaps (a Poisson process once the gaps are scaled by the mean gap)."""
+    assert text_bytes >= max_bytes
+    rng = rng_for(seed)
+    texts, starts = [], []
+    for mix in SCRIPTS:
+        for direction in (0, 1):
+            unit = "utf8" if direction == 0 else "utf16"
+            budget = text_bytes if direction == 0 else text_bytes // 2
+            cps, lens = draw_chars(rng, mix, budget, unit, with_sizes=True)
+            texts.append(to_utf8(cps) if direction == 0 else to_utf16(cps))
+            starts.append(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64))
+    sizes = np.exp(rng.uniform(np.log(min_bytes), np.log(max_bytes), n_requests)).astype(np.int64)
+    scripts = rng.integers(0, len(SCRIPTS), n_requests)
+    direction = rng.integers(0, 2, n_requests).astype(np.int8)
+    validate_only = rng.random(n_requests) < validate_frac
+    invalid = rng.random(n_requests) < invalid_frac
+    gaps = rng.exponential(1.0, n_requests)
+    source = (2 * scripts + direction).astype(np.int64)
+    offset = np.zeros(n_requests, np.int64)
+    units = np.zeros(n_requests, np.int64)
+    payloads = []
+    for i in range(n_requests):
+        t = int(source[i])
+        st, total = starts[t], texts[t].size
+        want = int(sizes[i]) if direction[i] == 0 else int(sizes[i]) // 2
+        last = int(np.searchsorted(st, total - want, side="right"))     # starts that leave room
+        k = int(rng.integers(0, max(last, 1)))
+        a = int(st[k])
+        b = int(st[np.searchsorted(st, a + want, side="right") - 1])    # whole characters only
+        offset[i], units[i] = a, b - a
+        if invalid[i]:
+            piece = texts[t][a:b]
+            inner = st[k:np.searchsorted(st, b, side="right")] - a     # boundaries inside the slice
+            j = int(inner[int(rng.integers(0, inner.size))])
+            if direction[i] == 0:
+                tok, _ = utf8_error_token(rng, UTF8_TOKEN_KINDS[int(rng.integers(0, len(UTF8_TOKEN_KINDS)))])
+                tok = np.frombuffer(tok, dtype=np.uint8)
+            else:
+                tok = np.array(utf16_error_token(rng)[0], dtype=np.uint16)
+            # the token goes in at boundary j; the slice keeps its length
+            p = np.concatenate([piece[:j], tok, piece[j:]])[:piece.size].astype(piece.dtype)
+            source[i], offset[i] = -1 - len(payloads), 0
+            payloads.append(p)
+    return ServeWorkload(texts, payloads, direction, validate_only, invalid, source, offset, units, gaps)

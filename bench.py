@@ -211,7 +211,7 @@ def run_gpu(args):
     import paper_2109_10433_gb300 as g
     g.build()
 
-    data = W.cjk_emoji_utf16_256mib(seed=1 + rank)
+    data = W.cjk_emoji_utf16_256mib(seed=1 + rank, nbytes=args.mib << 20)
     n = data.size
     inp = torch.from_numpy(data.view(np.int16)).to(dev)
     out = torch.empty(3 * n, dtype=torch.uint8, device=dev)
@@ -315,7 +315,8 @@ def run_gpu(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "input_bytes": int(data.nbytes),
+        "config": {"workload": WORKLOAD if args.mib == 256 else WORKLOAD.replace("256MiB", f"{args.mib}MiB"),
+                   "input_bytes": int(data.nbytes),
                    "output_bytes": int(out_bytes), "chars": chars,
                    "l2": "input (256 MiB) larger than L2, no flush",
                    "parallelism": f"replicas{world}"},
@@ -551,6 +552,9 @@ def main():
     ap.add_argument("--e2e-warmup", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mib", type=int, default=256,
+                    help="input MiB of the UTF-16 workload (256 is the measured configuration; "
+                         "smaller sizes are for profiler captures)")
     ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--budget-gb", type=int, default=8)

@@ -542,6 +542,83 @@ def run_serve(args):
     return 0
 
 
+def run_passes(args):
+    """Every kernel of the path on its own: the two transcoders and the four
+    validate / length passes, each timed per launch with CUDA events, with
+    achieved algorithmic bytes per second against the measured HBM peak.
+    UTF-16 input: the 256 MiB headline buffer (larger than L2).  UTF-8 input:
+    64 MiB of the 4-byte-heavy mix (40% U+10000-10FFFF, 30% U+0800-FFFF,
+    30% ASCII), valid; L2 is flushed (a 512 MB write) before every timed
+    launch."""
+    import torch
+
+    import paper_2109_10433_gb300 as g
+
+    g.build()
+    torch.cuda.set_device(0)
+    peak, peak_kind = measured_peak()
+    L = g.lib()
+    s = torch.cuda.current_stream()
+    sp = g._stream(s)
+    u16 = W.cjk_emoji_utf16_256mib(nbytes=args.mib << 20)
+    u8 = W.utf8_text(2, 64 << 20, W.MIX_FOUR_BYTE_HEAVY)
+    d16 = torch.from_numpy(u16.view(np.int16).copy()).cuda()
+    d8 = torch.from_numpy(u8.copy()).cuda()
+    n16, n8 = int(u16.size), int(u8.size)
+    out8 = torch.empty(3 * n16, dtype=torch.uint8, device="cuda")
+    out16 = torch.empty(n8, dtype=torch.int16, device="cuda")
+    ws = g.Workspace(max(n16, n8) + 16)
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    ln = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    len8 = g.utf8_length_from_utf16(d16, ws=ws)
+    len16 = g.utf16_length_from_utf8(d8, ws=ws)
+    cases = [
+        ("utf16_to_utf8", "utf16", lambda: L.gputf_utf16_to_utf8(g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr,
+                                                                 ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
+        ("validate_utf16", "utf16", lambda: L.gputf_validate_utf16(g._ptr(d16), n16, ws.ptr, ws.nbytes, g._ptr(res),
+                                                                   sp), 2 * n16),
+        ("utf8_length_from_utf16", "utf16", lambda: L.gputf_utf8_length_from_utf16(g._ptr(d16), n16, ws.ptr,
+                                                                                   ws.nbytes, g._ptr(ln), sp), 2 * n16),
+        ("utf8_to_utf16", "utf8", lambda: L.gputf_utf8_to_utf16(g._ptr(d8), n8, g._ptr(out16), n8, ws.ptr, ws.nbytes,
+                                                                g._ptr(res), sp), n8 + 2 * len16),
+        ("validate_utf8", "utf8", lambda: L.gputf_validate_utf8(g._ptr(d8), n8, ws.ptr, ws.nbytes, g._ptr(res), sp),
+         n8),
+        ("utf16_length_from_utf8", "utf8", lambda: L.gputf_utf16_length_from_utf8(g._ptr(d8), n8, ws.ptr, ws.nbytes,
+                                                                                   g._ptr(ln), sp), n8),
+    ]
+    rows = []
+    clocks = ClockSampler(None)
+    clocks.start()
+    for name, src, fn, algo in cases:
+        for _ in range(max(args.warmup, 3)):
+            if fn() != 0:
+                raise RuntimeError(name)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            if src == "utf8":
+                flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        us = statistics.median(ms) * 1e3
+        gbs = algo / (us * 1e-6) / 1e9
+        rows.append({"kernel": name, "input": "utf16 %d MiB cjk/emoji" % args.mib if src == "utf16"
+                     else "utf8 64 MiB four-byte-heavy", "input_bytes": (2 * n16 if src == "utf16" else n8),
+                     "algorithmic_bytes": int(algo), "median_us": us, "min_us": min(ms) * 1e3,
+                     "input_gbs": (2 * n16 if src == "utf16" else n8) / (us * 1e-6) / 1e9,
+                     "achieved_gbs": gbs, "frac": gbs / peak})
+    clk = clocks.stop()
+    print(json.dumps({"metric": "per-kernel algorithmic GB/s vs HBM roofline", "unit": "GB/s",
+                      "peak": peak, "peak_source": peak_kind, "steps": args.steps, "kernels": rows,
+                      "clocks": clk}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,7 +632,7 @@ def main():
     ap.add_argument("--mib", type=int, default=256,
                     help="input MiB of the UTF-16 workload (256 is the measured configuration; "
                          "smaller sizes are for profiler captures)")
-    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve"])
+    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve", "passes"])
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--budget-gb", type=int, default=8)
     ap.add_argument("--slots", type=int, default=4)
@@ -568,6 +645,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve" and args.impl != "reference":
         return run_serve(args)
+    if args.workload == "passes" and args.impl != "reference":
+        return run_passes(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -290,6 +290,23 @@ __device__ __forceinline__ uint64_t block_min(uint64_t v, unsigned long long *sc
     return m;
 }
 
+/* Block-wide sum of 64-bit values, returned to every thread; contains syncs. */
+template <int THREADS>
+__device__ __forceinline__ uint64_t block_sum(uint64_t v, unsigned long long *scratch)
+{
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    uint64_t m = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) m += scratch[w];
+    __syncthreads();
+    return m;
+}
+
 /* Marks this CTA done; returns true (to every thread) in the CTA that
  * finished last.  Everything the CTA wrote before is visible to that CTA. */
 __device__ __forceinline__ bool finish_cta(WsHeader *h, unsigned *smem_flag)

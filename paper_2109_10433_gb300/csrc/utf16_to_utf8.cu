@@ -147,8 +147,8 @@ struct U16Layout {
  *   phase A(n): bytes per unit, validation, block scan; publish n's aggregate
  *               (and its first error);
  *   phase B(c): c's exclusive output offset by decoupled look-back (its
- *               status words are requested first and examined after the
- *               bytes are written); c's bytes into the staging buffer at
+ *               status words are requested at the top of the iteration and
+ *               examined after the bytes are written); c's bytes into the staging buffer at
  *               tile-local offsets; publish c's inclusive prefix; write the
  *               tile out with aligned 16-byte stores;
  *   then take a new ticket and start its input copy into the freed stage.
@@ -223,6 +223,11 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 
 #define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
     for (int it = 0;; it++) {
+        /* the look-back window of tile c (the tiles before it) is requested
+         * first: its words arrive while phase A of tile n and the encoding
+         * of tile c run, and are examined after them */
+        const long long lb_idx = (long long)c_tile - 1 - tid;
+        const uint64_t lb_word = (have_c && c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
         /* ---------------- phase A of tile n ---------------- */
         const int sn = it % STAGES;
         const unsigned long long t = s_ring[sn];
@@ -301,10 +306,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         if (have_c) {
             const uint16_t *sb = stages + (size_t)c_stage * Lay::STAGE_UNITS;
             const int i0 = HALO16 + tid * UPT;
-            /* the look-back window's status words are requested now and
-             * examined after the bytes are written */
-            const long long lb_idx = (long long)c_tile - 1 - tid;
-            const uint64_t lb_word = (c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
 
             uint32_t w[WORDS];
 #pragma unroll
@@ -469,7 +470,44 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 
 /* ------------------------------------------------------------------------
  * Validate-only and length-only passes.
+ *
+ * Streaming kernels: a grid of resident CTAs walks the tiles (grid-stride);
+ * each thread holds its chunk of the current tile in registers and issues the
+ * loads of its chunk of the next tile before working on the current one, so
+ * that a tile's memory latency hides behind the previous tile's arithmetic.
+ * No barrier is taken per tile.
  * ---------------------------------------------------------------------- */
+
+/* Bit 15 of each 16-bit half: set when the half of x is zero.  Exact for
+ * halves that are multiples of 0x400 (a borrow out of a zero low half leaves
+ * such a high half's bit 15 clear unless it is zero too). */
+__device__ __forceinline__ uint32_t zero_halves(uint32_t x)
+{
+    return (x - 0x00010001u) & ~x & 0x80008000u;
+}
+
+/* Section 3's surrogate rule over a chunk: a high surrogate must be followed
+ * by a low one and a low one must follow a high one, i.e. for every two
+ * adjacent units, "the first is high" equals "the second is low".  Returns a
+ * nonzero word when some pair in the chunk (including the unit before it,
+ * pu, and the one after it, nu) breaks the rule. */
+template <int WORDS>
+__device__ __forceinline__ uint32_t surrogate_mismatch(const uint32_t (&w)[WORDS], uint32_t pu, uint32_t nu)
+{
+    uint32_t bad = 0;
+    uint32_t hcarry = is_high(pu) ? 0x8000u : 0u;   /* "high" of the unit before, at bit 15 */
+#pragma unroll
+    for (int k = 0; k < WORDS; k++) {
+        const uint32_t x = (w[k] & 0xFC00FC00u) ^ 0xD800D800u;   /* zero half: high surrogate */
+        const uint32_t hi = zero_halves(x);
+        const uint32_t lo = zero_halves(x ^ 0x04000400u);        /* zero half: low surrogate */
+        /* bit 15: pair (2k-1, 2k); bit 31: pair (2k, 2k+1) */
+        bad |= ((hi << 16) | hcarry) ^ lo;
+        hcarry = hi >> 16;
+    }
+    return bad | ((hcarry != 0) != is_low(nu));
+}
+
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
@@ -484,31 +522,36 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
     const uint16_t *base = in - head;
     const uint64_t endx = head + n;
     uint64_t first_err = NONE;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    uint64_t tile = blockIdx.x;
+    uint32_t w[WORDS];
+    if (tile < tiles) load_chunk16<WORDS>(base, tile * TILE + (uint64_t)tid * UPT, head, endx, w);
+    while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
-        uint32_t w[WORDS];
-        load_chunk16<WORDS>(base, e0, head, endx, w);
-        bool sur = false;
-#pragma unroll
-        for (int k = 0; k < WORDS; k++) sur |= has_surrogate(w[k]);
+        const uint64_t next = tile + gridDim.x;
+        uint32_t v[WORDS];
+        if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
         uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
         uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
         if (lane == 0) pu = unit_at(base, (long long)e0 - 1, head, endx);
         if (lane == 31) nu = unit_at(base, (long long)(e0 + UPT), head, endx);
-        if (sur && first_err == NONE) {
+        /* units outside the input read as zero, which is no surrogate, so a
+         * broken pair always has an input unit to blame */
+        if (surrogate_mismatch<WORDS>(w, pu, nu) && first_err == NONE) {
             uint32_t prev = pu;
 #pragma unroll
             for (int k = 0; k < UPT; k++) {
                 const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
-                const uint32_t next = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
-                const bool bad = (is_high(u) && !is_low(next)) || (is_low(u) && !is_high(prev));
+                const uint32_t nx = k + 1 < UPT ? (w[(k + 1) / 2] >> (16 * ((k + 1) & 1))) & 0xFFFF : nu;
+                const bool bad = (is_high(u) && !is_low(nx)) || (is_low(u) && !is_high(prev));
                 const long long ex = (long long)(e0 + k);
                 if (bad && ex >= (long long)head && ex < (long long)endx && first_err == NONE)
                     first_err = e0 + k - head;
                 prev = u;
             }
         }
-        if (__syncthreads_or(first_err != NONE)) break;
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = v[k];
+        tile = next;
     }
     if (__syncthreads_or(first_err != NONE)) {
         const uint64_t m = block_min<THREADS>(first_err, s_min);
@@ -525,6 +568,9 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
     reset_workspace(hdr, nullptr, 0);
 }
 
+/* UTF-8 length (Table 2): n + #(u >= 0x80) + #(u >= 0x800) - #surrogates, the
+ * three counts taken two units at a time.  A unit outside the input reads as
+ * zero and adds nothing. */
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles,
@@ -532,31 +578,40 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
 {
     constexpr int UPT = 2 * WORDS;
     constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
-    __shared__ uint32_t s_warp[THREADS / 32 + 1];
+    __shared__ unsigned long long s_part[THREADS / 32];
     __shared__ unsigned s_flag;
     const int tid = threadIdx.x;
     const uint64_t head = ((uintptr_t)in & 15) / 2;
     const uint16_t *base = in - head;
     const uint64_t endx = head + n;
-    uint32_t acc = 0;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
-        uint32_t w[WORDS];
-        const bool interior = load_chunk16<WORDS>(base, e0, head, endx, w);
+    uint64_t acc = 0;
+    uint64_t tile = blockIdx.x;
+    uint32_t w[WORDS];
+    if (tile < tiles) load_chunk16<WORDS>(base, tile * TILE + (uint64_t)tid * UPT, head, endx, w);
+    while (tile < tiles) {
+        const uint64_t next = tile + gridDim.x;
+        uint32_t v[WORDS];
+        if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
+        uint32_t up = 0, sur = 0;   /* per-half counts in bits 0-15 and 16-31 */
 #pragma unroll
-        for (int k = 0; k < UPT; k++) {
-            const uint32_t u = (w[k / 2] >> (16 * (k & 1))) & 0xFFFF;
-            const long long ex = (long long)(e0 + k);
-            const bool in_range = interior || (ex >= (long long)head && ex < (long long)endx);
-            const uint32_t l = u < 0x80 ? 1 : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2 : 3);
-            acc += in_range ? l : 0;
+        for (int k = 0; k < WORDS; k++) {
+            const uint32_t x = w[k];
+            /* a half >= 0x80: one of bits 7-15 set; >= 0x800: one of bits 11-15 */
+            const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+            const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+            const uint32_t s = zero_halves((x & 0xF800F800u) ^ 0xD800D800u);
+            up += (ge80 >> 15) + (ge800 >> 15);
+            sur += s >> 15;
         }
+        acc += (up & 0xFFFF) + (up >> 16) - (sur & 0xFFFF) - (sur >> 16);
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = v[k];
+        tile = next;
     }
-    uint32_t sum;
-    block_exclusive<THREADS>(acc, s_warp, &sum);
+    const uint64_t sum = block_sum<THREADS>(acc, s_part);
     if (tid == 0) atomicAdd(&hdr->accum, (unsigned long long)sum);
     if (!finish_cta(hdr, &s_flag)) return;
-    if (tid == 0) *len_out = ld_relaxed(&hdr->accum);
+    if (tid == 0) *len_out = ld_relaxed(&hdr->accum) + n;
     reset_workspace(hdr, nullptr, 0);
 }
 
@@ -595,9 +650,17 @@ cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, u
     return cudaGetLastError();
 }
 
-static unsigned pass_grid16(uint64_t tiles, int sms)
+/* Grid of a streaming pass: the CTAs that fit on the device at once (no
+ * more than there are tiles). */
+template <typename K>
+static unsigned resident_grid(K kern, int threads, uint64_t tiles, int sms, int *per_sm)
 {
-    uint64_t g = (uint64_t)sms * 8;
+    if (*per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, 0) != cudaSuccess || b < 1) b = 1;
+        *per_sm = b;
+    }
+    const uint64_t g = (uint64_t)sms * *per_sm;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
 }
 
@@ -607,8 +670,10 @@ cudaError_t launch_validate_utf16(const uint16_t *in, uint64_t n, void *ws, DevR
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 2 * W;
     const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
-    validate_utf16_kernel<T, W><<<pass_grid16(tiles, sms), T, 0, stream>>>(
-        in, n, tiles, static_cast<WsHeader *>(ws), res);
+    static int per_sm = 0;
+    auto kern = validate_utf16_kernel<T, W>;
+    kern<<<resident_grid(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
+                                                                         res);
     return cudaGetLastError();
 }
 
@@ -618,8 +683,10 @@ cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 2 * W;
     const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
-    utf8_length_from_utf16_kernel<T, W><<<pass_grid16(tiles, sms), T, 0, stream>>>(
-        in, n, tiles, static_cast<WsHeader *>(ws), len);
+    static int per_sm = 0;
+    auto kern = utf8_length_from_utf16_kernel<T, W>;
+    kern<<<resident_grid(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
+                                                                         len);
     return cudaGetLastError();
 }
 

@@ -457,6 +457,9 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
 /* ------------------------------------------------------------------------
  * Validate-only and length-only passes: one read of the input, no scan.
  * ---------------------------------------------------------------------- */
+/* Streaming passes: a grid of resident CTAs walks the tiles (grid-stride);
+ * each thread issues the loads of its chunk of the next tile before working
+ * on the current one, and no barrier is taken per tile. */
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
@@ -471,15 +474,22 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;
     uint64_t first_err = NONE;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    uint64_t tile = blockIdx.x;
+    uint32_t w[WORDS];
+    bool interior = false;
+    if (tile < tiles) interior = load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
+    while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
-        uint32_t w[WORDS];
-        const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
+        const uint64_t next = tile + gridDim.x;
+        uint32_t v[WORDS];
+        bool v_interior = false;
+        if (next < tiles) v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
         uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
         if (lane == 0) pw = word_at(base, (long long)e0 - 4, head, endx);
         uint32_t any = pw;
 #pragma unroll
         for (int k = 0; k < WORDS; k++) any |= w[k];
+        /* all-ASCII chunks (and the word before them) hold no error */
         if ((any & 0x80808080u) != 0 && first_err == NONE) {
 #pragma unroll
             for (int k = WORDS - 1; k >= 0; k--) {
@@ -488,7 +498,10 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
                 if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
             }
         }
-        if (__syncthreads_or(first_err != NONE)) break;   /* later tiles cannot hold an earlier error */
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = v[k];
+        interior = v_interior;
+        tile = next;
     }
     if (__syncthreads_or(first_err != NONE)) {
         const uint64_t m = block_min<THREADS>(first_err, s_min);
@@ -508,6 +521,8 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
     reset_workspace(hdr, nullptr, 0);
 }
 
+/* UTF-16 length of UTF-8 input (Table 2): one unit per byte that is not a
+ * continuation byte, one more per byte >= 0xF0. */
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
@@ -515,33 +530,43 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
 {
     constexpr int BPT = 4 * WORDS;
     constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
-    __shared__ uint32_t s_warp[THREADS / 32 + 1];
+    __shared__ unsigned long long s_part[THREADS / 32];
     __shared__ unsigned s_flag;
     const int tid = threadIdx.x;
     const uint64_t head = (uintptr_t)in & 15;
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;
     uint64_t acc = 0;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    uint64_t tile = blockIdx.x;
+    uint32_t w[WORDS];
+    bool interior = false;
+    if (tile < tiles) interior = load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
+    while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
-        uint32_t w[WORDS];
-        const bool interior = load_chunk8<WORDS>(base, e0, head, endx, w);
+        const uint64_t next = tile + gridDim.x;
+        uint32_t v[WORDS];
+        bool v_interior = false;
+        if (next < tiles) v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
+        uint32_t c = 0;
 #pragma unroll
         for (int k = 0; k < WORDS; k++) {
             const uint32_t x = w[k];
-            uint32_t lead = ~(x & ~(x << 1)) & 0x80808080u;
-            uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
+            uint32_t lead = ~(x & ~(x << 1)) & 0x80808080u;            /* not 10xxxxxx */
+            uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;   /* 1111xxxx */
             if (!interior) {
                 const uint32_t rm = range_mask((long long)(e0 + 4 * k), head, endx, false);
                 lead &= rm;
                 f4 &= rm;
             }
-            acc += __popc(lead) + __popc(f4);
+            c += __popc(lead) + __popc(f4);
         }
+        acc += c;
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = v[k];
+        interior = v_interior;
+        tile = next;
     }
-    /* per-thread counts stay below 2^32 for one CTA's share of any input */
-    uint32_t sum;
-    block_exclusive<THREADS>((uint32_t)acc, s_warp, &sum);
+    const uint64_t sum = block_sum<THREADS>(acc, s_part);
     if (tid == 0) atomicAdd(&hdr->accum, (unsigned long long)sum);
     if (!finish_cta(hdr, &s_flag)) return;
     if (tid == 0) *len_out = ld_relaxed(&hdr->accum);
@@ -585,9 +610,17 @@ cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, u
     return cudaGetLastError();
 }
 
-static unsigned pass_grid(uint64_t tiles, int device_sms)
+/* Grid of a streaming pass: the CTAs that fit on the device at once (no
+ * more than there are tiles). */
+template <typename K>
+static unsigned resident_grid8(K kern, int threads, uint64_t tiles, int sms, int *per_sm)
 {
-    uint64_t g = (uint64_t)device_sms * 8;
+    if (*per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, 0) != cudaSuccess || b < 1) b = 1;
+        *per_sm = b;
+    }
+    const uint64_t g = (uint64_t)sms * *per_sm;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
 }
 
@@ -597,8 +630,10 @@ cudaError_t launch_validate_utf8(const uint8_t *in, uint64_t n, void *ws, DevRes
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 4 * W;
     const uint64_t tiles = ((uintptr_t)in % 16 + n + 1 + TILE - 1) / TILE;
-    validate_utf8_kernel<T, W><<<pass_grid(tiles, sms), T, 0, stream>>>(
-        in, n, tiles, static_cast<WsHeader *>(ws), res);
+    static int per_sm = 0;
+    auto kern = validate_utf8_kernel<T, W>;
+    kern<<<resident_grid8(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
+                                                                          res);
     return cudaGetLastError();
 }
 
@@ -608,8 +643,10 @@ cudaError_t launch_utf16_length_from_utf8(const uint8_t *in, uint64_t n, void *w
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 4 * W;
     const uint64_t tiles = ((uintptr_t)in % 16 + n + TILE - 1) / TILE;
-    utf16_length_from_utf8_kernel<T, W><<<pass_grid(tiles, sms), T, 0, stream>>>(
-        in, n, tiles, static_cast<WsHeader *>(ws), len);
+    static int per_sm = 0;
+    auto kern = utf16_length_from_utf8_kernel<T, W>;
+    kern<<<resident_grid8(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
+                                                                          len);
     return cudaGetLastError();
 }
 

@@ -278,3 +278,38 @@ def test_four_byte_heavy_utf8_64mib_every_error(g, ws):
     assert tuple(res) == tuple(ref) and res.error == oracle.OK
     assert np.array_equal(out[:res.written].cpu().numpy().view(np.uint16), ref_out)
     assert g.utf16_length_from_utf8(dev_u8(clean), ws=ws) == ref.written
+
+
+def test_validate_utf16_one_error_anywhere_in_a_long_buffer(g, ws):
+    """The validate-only pass checks surrogate pairs two units at a time and
+    streams several tiles per CTA: one lone or broken surrogate placed at
+    thread (16 units), warp (512), tile (4096) boundaries and in tiles a CTA
+    reaches only after prefetching is found at its exact position."""
+    base = W.utf16_text(31, 6 << 20, W.MIX_CJK_EMOJI)
+    n = base.size
+    positions = []
+    for b in (16 * 7, 512 * 3, 4096 * 5, 4096 * 1500, n - 4096 * 3, n - 2):
+        positions += [b - 1, b, b + 1]
+    positions += [0, n - 1, 15, 31, 32]
+    for form in range(3):
+        for p in positions:
+            d = base.copy()
+            if form == 0:      # a lone high surrogate
+                d[p] = 0xD83D
+                if p + 1 < n:
+                    d[p + 1] = 0x4E00
+            elif form == 1:    # a lone low surrogate
+                d[p] = 0xDE00
+                if p > 0:
+                    d[p - 1] = 0x4E00
+            else:              # a high followed by a low in the wrong order
+                d[p] = 0xDE00
+                if p + 1 < n:
+                    d[p + 1] = 0xD83D
+                if p > 0:
+                    d[p - 1] = 0x4E00
+                if p + 2 < n:
+                    d[p + 2] = 0x4E00
+            inp = dev_u16(d, p % 8)
+            assert tuple(g.validate_utf16(inp, ws=ws)) == tuple(oracle.validate_utf16(d)), (form, p)
+            assert g.utf8_length_from_utf16(inp, ws=ws) == oracle.utf8_length_from_utf16(d), (form, p)

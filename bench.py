@@ -134,6 +134,29 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def slowest(value: float, device) -> float:
+    """The largest of every rank's value (the slowest rank's time); the value
+    itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_gbs(world: int, bytes_per_rank_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's bytes over
+    the slowest rank's time."""
+    return world * steps * bytes_per_rank_step / seconds / 1e9
+
+
+def rank_seed(rank: int) -> int:
+    """Each replica transcodes its own buffer of the same mix."""
+    return 1 + rank
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -211,7 +234,7 @@ def run_gpu(args):
     import paper_2109_10433_gb300 as g
     g.build()
 
-    data = W.cjk_emoji_utf16_256mib(seed=1 + rank, nbytes=args.mib << 20)
+    data = W.cjk_emoji_utf16_256mib(seed=rank_seed(rank), nbytes=args.mib << 20)
     n = data.size
     inp = torch.from_numpy(data.view(np.int16)).to(dev)
     out = torch.empty(3 * n, dtype=torch.uint8, device=dev)
@@ -266,12 +289,9 @@ def run_gpu(args):
 
     region_ms = region0.elapsed_time(region1)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if world > 1:
-        t = torch.tensor([region_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        region_ms = float(t.item())
+    region_ms = slowest(region_ms, dev)
     ms_per_step = region_ms / args.steps
-    value = world * args.steps * data.nbytes / (region_ms * 1e-3) / 1e9
+    value = replica_gbs(world, data.nbytes, args.steps, region_ms * 1e-3)
 
     # end to end through the host-buffer C-ABI call: pinned host input in,
     # UTF-8 out to pinned host memory, result read back every step
@@ -286,12 +306,8 @@ def run_gpu(args):
         assert rr.error == 0 and rr.written == out_bytes
         if i >= args.e2e_warmup:
             e2e_times.append(el)
-    e2e_total = max(sum(e2e_times), 1e-12)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_val = world * len(e2e_times) * data.nbytes / e2e_total / 1e9 if e2e_times else None
+    e2e_total = slowest(max(sum(e2e_times), 1e-12), dev)
+    e2e_val = replica_gbs(world, data.nbytes, len(e2e_times), e2e_total) if e2e_times else None
 
     if rank != 0:
         torch.distributed.destroy_process_group()

@@ -79,6 +79,20 @@ __device__ __forceinline__ bool has_surrogate(uint32_t x)
     return ((y - 0x00010001u) & ~y & 0x80008000u) != 0;
 }
 
+/* Bit 15 of each 16-bit half: set when the half of x is zero.  Exact for
+ * halves that are multiples of 0x400 (a borrow out of a zero low half leaves
+ * such a high half's bit 15 clear unless it is zero too). */
+__device__ __forceinline__ uint32_t zero_halves(uint32_t x)
+{
+    return (x - 0x00010001u) & ~x & 0x80008000u;
+}
+
+/* Sum of the eight 4-bit fields of x (each at most 8). */
+__device__ __forceinline__ uint32_t nibble_sum(uint32_t x)
+{
+    return (((x & 0x0F0F0F0Fu) + ((x >> 4) & 0x0F0F0F0Fu)) * 0x01010101u) >> 24;
+}
+
 /* Append `len` bytes held in `v` to a thread's run of staged bytes.  Full
  * words are stored; the first word (when the run starts inside a word) and
  * the last partial word are shared with the neighbouring threads' runs and
@@ -172,7 +186,8 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
     constexpr int WORDS = UPT / 2;
-    static_assert(UPT == 16, "16 units per thread: two words of 4-bit byte counts");
+    constexpr int NW = UPT / 8;   /* words of 4-bit per-unit byte counts */
+    static_assert(UPT % 8 == 0 && UPT <= 32, "units per thread: a multiple of 8, at most 32");
     static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
     extern __shared__ uint4 smem4[];
     uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
@@ -218,7 +233,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     /* state of tile c (phase A done, phase B pending) */
     bool have_c = false;
     unsigned long long c_tile = 0;
-    uint32_t c_total = 0, c_excl = 0, c_la = 0, c_lb = 0;
+    uint32_t c_total = 0, c_excl = 0, c_nib[NW];
+#pragma unroll
+    for (int j = 0; j < NW; j++) c_nib[j] = 0;
     int c_stage = 0;
 
 #define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
@@ -232,7 +249,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         const int sn = it % STAGES;
         const unsigned long long t = s_ring[sn];
         const bool have_n = t < tiles;
-        uint32_t n_total = 0, n_excl = 0, n_la = 0, n_lb = 0;
+        uint32_t n_total = 0, n_excl = 0, n_nib[NW];
+#pragma unroll
+        for (int j = 0; j < NW; j++) n_nib[j] = 0;
         if (have_n) {
             const uint64_t x0 = t * TILE;
             uint16_t *sb = stages + (size_t)sn * Lay::STAGE_UNITS;
@@ -256,40 +275,52 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             }
             const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
-            uint32_t inr = 0xFFFFu;
-            if (!interior) {
+            /* bytes per unit, two units per step (Table 2, with a surrogate
+             * pair written whole by its high unit): 1 + [u >= 0x80] +
+             * [u >= 0x800] + [high] - 3 [low], i.e. 4 for a high unit, 0 for
+             * a low one and len8 for the rest; and Section 3's pairing rule
+             * read as "the unit before is high" == "this unit is low" for
+             * every two adjacent units */
+            uint32_t lanes = 0, bad = 0, hcarry = is_high(pu) ? 0x8000u : 0u;
+#pragma unroll
+            for (int k = 0; k < WORDS; k++) {
+                const uint32_t x = w[k];
+                const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+                const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+                const uint32_t sg = (x & 0xFC00FC00u) ^ 0xD800D800u;
+                const uint32_t hi = zero_halves(sg), lo = zero_halves(sg ^ 0x04000400u);
+                /* per-half byte counts (0..4) in bits 0-2 and 16-18 */
+                const uint32_t L = 0x00010001u + (ge80 >> 15) + (ge800 >> 15) + (hi >> 15) - 3u * (lo >> 15);
+                lanes += L;
+                n_nib[k / 4] |= ((L | (L >> 12)) & 0xFFu) << (8 * (k % 4));
+                bad |= ((hi << 16) | hcarry) ^ lo;   /* bit 15: pair (2k-1, 2k); bit 31: (2k, 2k+1) */
+                hcarry = hi >> 16;
+            }
+            bad |= (uint32_t)((hcarry != 0) != is_low(nu));
+            n_total = (lanes & 0xFFFF) + (lanes >> 16);
+            uint32_t inr = 0xFFFFFFFFu;
+            if (!interior) {   /* units outside the input write nothing */
                 inr = 0;
 #pragma unroll
                 for (int k = 0; k < UPT; k++)
                     inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
-            }
-            /* bytes per unit (4-bit fields) and surrogate positions */
-            uint32_t himask = 0, lomask = 0;
+                n_total = 0;
 #pragma unroll
-            for (int k = 0; k < UPT; k++) {
-                const uint32_t u = UNIT(k);
-                uint32_t l = len8(u);
-                if (!interior) l = ((inr >> k) & 1) ? l : 0;
-                if (k < 8) n_la |= l << (4 * k);
-                else n_lb |= l << (4 * (k - 8));
-                n_total += l;
-                himask |= is_high(u) ? (1u << k) : 0u;
-                lomask |= is_low(u) ? (1u << k) : 0u;
+                for (int j = 0; j < NW; j++) {
+                    n_nib[j] &= spread4(inr >> (8 * j)) * 0xFu;
+                    n_total += nibble_sum(n_nib[j]);
+                }
             }
             uint64_t first_err = NONE;
-            if ((himask | lomask) & inr) {
-                const uint32_t lo_next = (lomask >> 1) | (is_low(nu) ? (1u << (UPT - 1)) : 0u);   /* bit k: unit k+1 is low */
-                const uint32_t prev_hi = (himask << 1) | (is_high(pu) ? 1u : 0u);    /* bit k: unit k-1 is high */
-                /* Section 3: a high unit must be followed by a low one, a
-                 * low unit must follow a high one */
-                const uint32_t errs = ((himask & ~lo_next) | (lomask & ~prev_hi)) & inr;
-                if (errs) first_err = (uint64_t)(e0 + __ffs(errs) - 1) - head;
-                /* a pair is written whole by its high unit */
-                const uint32_t ps = himask & lo_next & inr, pe = lomask & prev_hi & inr;
-                if (ps | pe) {
-                    n_la += 2 * spread4(ps) - 2 * spread4(pe);
-                    n_lb += 2 * spread4(ps >> 8) - 2 * spread4(pe >> 8);
-                    n_total += 2 * (uint32_t)__popc(ps) - 2 * (uint32_t)__popc(pe);
+            if (bad) {   /* some pair breaks the rule: find the first invalid unit of the chunk */
+                uint32_t prev = pu;
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    const uint32_t nx = k + 1 < UPT ? UNIT(k + 1) : nu;
+                    const bool e = (is_high(u) && !is_low(nx)) || (is_low(u) && !is_high(prev));
+                    if (e && ((inr >> k) & 1) && first_err == NONE) first_err = (uint64_t)(e0 + k) - head;
+                    prev = u;
                 }
             }
             bool any_err;
@@ -321,7 +352,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             uint32_t o = c_excl;
 #pragma unroll
             for (int k = 0; k < UPT; k++) {
-                const uint32_t l = ((k < 8 ? c_la >> (4 * k) : c_lb >> (4 * (k - 8)))) & 0xF;
+                const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
                 put_utf8(outb, o, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
                 o += l;
             }
@@ -399,7 +430,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 uint64_t g = G0 + c_excl;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
-                    const uint32_t l = ((k < 8 ? c_la >> (4 * k) : c_lb >> (4 * (k - 8)))) & 0xF;
+                    const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
                     if (l && g + l > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
                     g += l;
                 }
@@ -416,8 +447,8 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         c_tile = t;
         c_total = n_total;
         c_excl = n_excl;
-        c_la = n_la;
-        c_lb = n_lb;
+#pragma unroll
+        for (int j = 0; j < NW; j++) c_nib[j] = n_nib[j];
         c_stage = sn;
         __syncthreads();
     }
@@ -477,14 +508,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
  * that a tile's memory latency hides behind the previous tile's arithmetic.
  * No barrier is taken per tile.
  * ---------------------------------------------------------------------- */
-
-/* Bit 15 of each 16-bit half: set when the half of x is zero.  Exact for
- * halves that are multiples of 0x400 (a borrow out of a zero low half leaves
- * such a high half's bit 15 clear unless it is zero too). */
-__device__ __forceinline__ uint32_t zero_halves(uint32_t x)
-{
-    return (x - 0x00010001u) & ~x & 0x80008000u;
-}
 
 /* Section 3's surrogate rule over a chunk: a high surrogate must be followed
  * by a low one and a low one must follow a high one, i.e. for every two
@@ -619,7 +642,7 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
  * Launchers.
  * ---------------------------------------------------------------------- */
 constexpr int U16_THREADS = 256;
-constexpr int U16_UPT = 16;     /* 4096-unit tiles */
+constexpr int U16_UPT = 24;     /* 6144-unit tiles */
 constexpr int U16_STAGES = 3;
 using U16Lay = U16Layout<U16_THREADS, U16_UPT, U16_STAGES>;
 

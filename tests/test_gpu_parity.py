@@ -17,7 +17,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TILE8 = 4096      # input bytes per tile, UTF-8 -> UTF-16
-TILE16 = 4096     # input units per tile, UTF-16 -> UTF-8
+TILE16 = 6144     # input units per tile, UTF-16 -> UTF-8 (24 units per thread)
+PASS16 = 4096     # input units per tile of the UTF-16 validate / length passes (16 per thread)
 GUARD = 0x5A
 
 
@@ -124,11 +125,12 @@ def test_sizes_around_tile_boundaries(g, ws):
             for off in (0, 1, 7, 15):
                 d8 = W.utf8_text(n + off, n, MIXES[(k + delta) % len(MIXES)])
                 check_8to16(g, ws, d8, in_off=off, out_off=int(rng.integers(0, 8)))
-            d16 = W.utf16_text(n, k * TILE16 + delta, MIXES[(k - delta) % len(MIXES)])
-            for off in (0, 1, 5, 7):
-                check_16to8(g, ws, d16, in_off=off, out_off=int(rng.integers(0, 16)))
+            for T16 in (TILE16, PASS16):
+                d16 = W.utf16_text(n, k * T16 + delta, MIXES[(k - delta) % len(MIXES)])
+                for off in (0, 1, 5, 7):
+                    check_16to8(g, ws, d16, in_off=off, out_off=int(rng.integers(0, 16)))
+                check_passes16(g, ws, d16)
             check_passes8(g, ws, d8)
-            check_passes16(g, ws, d16)
 
 
 def test_random_bytes_and_units(g, ws):
@@ -164,7 +166,8 @@ def test_every_utf8_error_class_around_tile_boundaries(g, ws, kind):
 def test_every_utf16_error_form_around_tile_boundaries(g, ws):
     rng = W.rng_for(19)
     base = W.utf16_text(6, 3 * TILE16 + 50, W.MIX_CJK_EMOJI)
-    for pos in list(range(TILE16 - 6, TILE16 + 6)) + list(range(2 * TILE16 - 6, 2 * TILE16 + 6)) + [0, 1, base.size - 1]:
+    near = [b + d for b in (TILE16, 2 * TILE16, PASS16, 24 * 5, 24 * 32, 16 * 9) for d in range(-6, 6)]
+    for pos in near + [0, 1, base.size - 1]:
         tok, _ = W.utf16_error_token(rng)
         d = np.concatenate([base[:pos], np.array(tok, np.uint16), base[pos:]])
         check_16to8(g, ws, d, in_off=pos % 8)

@@ -294,19 +294,22 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     }
                 }
             } else {
+                /* one bit per character start of the chunk; each step reads the
+                 * four bytes at the start from the stage */
+                uint32_t lm = 0;
 #pragma unroll
-                for (int k = 0; k < WORDS; k++) {
-                    const uint32_t nxt = k + 1 < WORDS ? w[k + 1] : nw;
-                    uint32_t m = lead[k];
-                    while (m) {
-                        const int j = first_byte(m);
-                        m &= m - 1;
-                        uint32_t u0, u1;
-                        const int c = decode_utf8(gputf_fshr(w[k], nxt, 8 * j), &u0, &u1);
-                        out16[o] = (uint16_t)u0;
-                        if (c == 2) out16[o + 1] = (uint16_t)u1;
-                        o += c;
-                    }
+                for (int k = 0; k < WORDS; k++)
+                    lm |= ((((lead[k] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+                const uint8_t *row = sb + i0;
+                while (lm) {
+                    const int p = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + (p & ~3));
+                    uint32_t u0, u1;
+                    const int c = decode_utf8(__funnelshift_r(wp[0], wp[1], 8 * (p & 3)), &u0, &u1);
+                    out16[o] = (uint16_t)u0;
+                    if (c == 2) out16[o + 1] = (uint16_t)u1;
+                    o += c;
                 }
             }
 
@@ -577,7 +580,7 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
  * Launchers.
  * ---------------------------------------------------------------------- */
 constexpr int U8_THREADS = 256;
-constexpr int U8_WORDS = 4;     /* 16 bytes per thread, 4 KiB tiles */
+constexpr int U8_WORDS = 8;     /* 32 bytes per thread, 8 KiB tiles */
 constexpr int U8_STAGES = 3;
 using U8Lay = U8Layout<U8_THREADS, U8_WORDS, U8_STAGES>;
 

@@ -16,7 +16,7 @@ import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TILE8 = 4096      # input bytes per tile, UTF-8 -> UTF-16
+TILE8 = 8192      # input bytes per tile, UTF-8 -> UTF-16 and the UTF-8 passes (32 per thread)
 TILE16 = 6144     # input units per tile, UTF-16 -> UTF-8 (24 units per thread)
 PASS16 = 4096     # input units per tile of the UTF-16 validate / length passes (16 per thread)
 GUARD = 0x5A

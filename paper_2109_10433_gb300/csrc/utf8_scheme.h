@@ -90,11 +90,11 @@ GPUTF_HD uint32_t gputf_fshr(uint32_t lo, uint32_t hi, uint32_t s)
 }
 
 /* Pack the four nibbles held in the low halves of the bytes of x into a
- * 16-bit PRMT selector (nibble k = byte k). */
+ * 16-bit PRMT selector (nibble k = byte k); bits 16-31 are zero. */
 GPUTF_HD uint32_t gputf_pack_nibbles(uint32_t x)
 {
     uint32_t y = x | (x >> 4);
-    return gputf_prmt(y, 0, 0x0020);
+    return gputf_prmt(y, 0, 0x4420);
 }
 
 /* 16-entry table lookup: sel = packed indexes, m = 0xFF in each byte whose
@@ -107,31 +107,61 @@ GPUTF_HD uint32_t gputf_lut16(uint32_t sel, uint32_t m, uint32_t q0, uint32_t q1
     return (hi & m) | (lo & ~m);
 }
 
-/* Error flags of the four bytes of w (nonzero byte k: byte k of w flagged),
- * given p, the four bytes just before w. */
+#if GPUTF_T1_W0 != GPUTF_T1_W1 || GPUTF_T3_W0 != GPUTF_T3_W1 || \
+    (GPUTF_T1_W0 & 0xFF) * 0x01010101u != GPUTF_T1_W0 || (GPUTF_T3_W0 & 0xFF) * 0x01010101u != GPUTF_T3_W0
+#error "T1 and T3 must be constant over indexes 0-7 (one PRMT per lookup below)"
+#endif
+
+/* What the check of a word needs from the word before it: the word, its
+ * bytes' high and low nibbles packed as PRMT selectors, and bit 7 of each
+ * byte set where the byte is >= 0xE0 (e0) or >= 0xF0 (f0). */
+typedef struct gputf_u8state {
+    uint32_t w, hi, lo, e0, f0;
+} gputf_u8state;
+
+GPUTF_HD gputf_u8state gputf_u8state_of(uint32_t w)
+{
+    gputf_u8state s;
+    s.w = w;
+    s.hi = gputf_pack_nibbles((w >> 4) & 0x0F0F0F0Fu);
+    s.lo = gputf_pack_nibbles(w & 0x0F0F0F0Fu);
+    s.e0 = w & (w << 1) & (w << 2);
+    s.f0 = s.e0 & (w << 3);
+    return s;
+}
+
+/* Error flags of the four bytes of w (nonzero byte k: byte k of w flagged)
+ * given the state of the four bytes just before w; the state moves on to
+ * w.  Byte k is checked against the byte before it through the three
+ * nibble tables (T1[p >> 4] & T2[p & 15] & T3[c >> 4]); bit 7 of the
+ * result (the two-continuations term) is then compared with "two bytes back
+ * >= 0xE0 or three bytes back >= 0xF0".  The selectors and the >= masks of
+ * the bytes before w are w's own, shifted by one nibble or byte with the
+ * previous word's carried in.  T1 and T3 are constant over indexes 0-7, so
+ * each takes one PRMT over entries 8-15. */
+GPUTF_HD uint32_t gputf_utf8_errors_step(gputf_u8state *st, uint32_t w)
+{
+    const gputf_u8state c = gputf_u8state_of(w);
+    const uint32_t prev1 = gputf_fshl(st->w, w, 8);            /* byte k: the byte before w.k */
+    const uint32_t sel_p_hi = (c.hi << 4) | (st->hi >> 12);
+    const uint32_t sel_p_lo = (c.lo << 4) | (st->lo >> 12);
+    const uint32_t m_p_hi = gputf_prmt(prev1, 0, 0xBA98);       /* p >> 4 >= 8  */
+    const uint32_t m_p_lo = gputf_prmt(prev1 << 4, 0, 0xBA98);  /* p & 15 >= 8  */
+    const uint32_t m_c_hi = gputf_prmt(w, 0, 0xBA98);           /* c >> 4 >= 8  */
+    const uint32_t t1 = (gputf_prmt(GPUTF_T1_W2, GPUTF_T1_W3, sel_p_hi ^ 0x8888) & m_p_hi) | (GPUTF_T1_W0 & ~m_p_hi);
+    const uint32_t t2 = gputf_lut16(sel_p_lo, m_p_lo, GPUTF_T2_W0, GPUTF_T2_W1, GPUTF_T2_W2, GPUTF_T2_W3);
+    const uint32_t t3 = (gputf_prmt(GPUTF_T3_W2, GPUTF_T3_W3, c.hi ^ 0x8888) & m_c_hi) | (GPUTF_T3_W0 & ~m_c_hi);
+    /* bit 7 of each byte: byte two back >= 0xE0, or three back >= 0xF0 */
+    const uint32_t must23 = (gputf_fshl(st->e0, c.e0, 16) | gputf_fshl(st->f0, c.f0, 24)) & 0x80808080u;
+    *st = c;
+    return (t1 & t2 & t3) ^ must23;
+}
+
+/* Error flags of the four bytes of w given p, the four bytes just before w. */
 GPUTF_HD uint32_t gputf_utf8_errors(uint32_t p, uint32_t w)
 {
-    uint32_t prev1 = gputf_fshl(p, w, 8);     /* byte k: the byte before w.k   */
-    uint32_t prev2 = gputf_fshl(p, w, 16);    /* byte k: two bytes before w.k  */
-    uint32_t prev3 = gputf_fshl(p, w, 24);    /* byte k: three bytes before    */
-
-    uint32_t sel_p_hi = gputf_pack_nibbles((prev1 >> 4) & 0x0F0F0F0Fu);
-    uint32_t sel_p_lo = gputf_pack_nibbles(prev1 & 0x0F0F0F0Fu);
-    uint32_t sel_c_hi = gputf_pack_nibbles((w >> 4) & 0x0F0F0F0Fu);
-    uint32_t m_p_hi = gputf_prmt(prev1, 0, 0xBA98);        /* p >> 4 >= 8  */
-    uint32_t m_p_lo = gputf_prmt(prev1 << 4, 0, 0xBA98);   /* p & 15 >= 8  */
-    uint32_t m_c_hi = gputf_prmt(w, 0, 0xBA98);            /* c >> 4 >= 8  */
-
-    uint32_t e = gputf_lut16(sel_p_hi, m_p_hi, GPUTF_T1_W0, GPUTF_T1_W1, GPUTF_T1_W2, GPUTF_T1_W3)
-               & gputf_lut16(sel_p_lo, m_p_lo, GPUTF_T2_W0, GPUTF_T2_W1, GPUTF_T2_W2, GPUTF_T2_W3)
-               & gputf_lut16(sel_c_hi, m_c_hi, GPUTF_T3_W0, GPUTF_T3_W1, GPUTF_T3_W2, GPUTF_T3_W3);
-
-    /* bit 7 of each byte: byte two back >= 0xE0, or three back >= 0xF0 */
-    uint32_t ge_e0 = prev2 & (prev2 << 1) & (prev2 << 2);
-    uint32_t ge_f0 = prev3 & (prev3 << 1) & (prev3 << 2) & (prev3 << 3);
-    uint32_t must23 = (ge_e0 | ge_f0) & 0x80808080u;
-
-    return (e & 0x7F7F7F7Fu) | ((e ^ must23) & 0x80808080u);
+    gputf_u8state st = gputf_u8state_of(p);
+    return gputf_utf8_errors_step(&st, w);
 }
 
 /* Bit 7 of each byte set iff that byte of x is nonzero. */
@@ -199,18 +229,17 @@ GPUTF_HD int gputf_utf8_fixup(const uint8_t *in, uint64_t n, uint64_t f, int *cl
  * before the buffer and from n on read as zero. */
 GPUTF_HD uint64_t gputf_utf8_first_flag(const uint8_t *in, uint64_t n)
 {
-    uint32_t p = 0;
+    gputf_u8state st = gputf_u8state_of(0);
     for (uint64_t base = 0; base <= n; base += 4) {
         uint32_t w = 0;
         for (int k = 0; k < 4; k++)
             if (base + k < n) w |= (uint32_t)in[base + k] << (8 * k);
-        uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(p, w));
+        uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors_step(&st, w));
         while (nz) {
             int k = (int)((__builtin_ctz(nz) - 7) / 8);
             if (base + (uint64_t)k <= n) return base + (uint64_t)k;
             nz &= nz - 1;
         }
-        p = w;
     }
     return UINT64_MAX;
 }

@@ -239,11 +239,20 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             const bool ascii = (any & 0x80808080u) == 0;
             uint64_t first_err = NONE;
             if (!__all_sync(FULL_MASK, ascii) && !ascii) {
+                gputf_u8state st = gputf_u8state_of(pw);
+                uint32_t errs[WORDS], anyerr = 0;
 #pragma unroll
-                for (int k = WORDS - 1; k >= 0; k--) {
-                    uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
-                    if (!interior) nz &= range_mask(e0 + 4 * k, head, endx, true);
-                    if (nz) first_err = (uint64_t)(e0 + 4 * k + first_byte(nz)) - head;
+                for (int k = 0; k < WORDS; k++) {
+                    errs[k] = gputf_utf8_errors_step(&st, w[k]);
+                    anyerr |= errs[k];
+                }
+                if (anyerr) {   /* the first flagged byte of the chunk */
+#pragma unroll
+                    for (int k = WORDS - 1; k >= 0; k--) {
+                        uint32_t nz = gputf_nonzero_bytes(errs[k]);
+                        if (!interior) nz &= range_mask(e0 + 4 * k, head, endx, true);
+                        if (nz) first_err = (uint64_t)(e0 + 4 * k + first_byte(nz)) - head;
+                    }
                 }
             }
             bool any_err;
@@ -494,11 +503,20 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
         for (int k = 0; k < WORDS; k++) any |= w[k];
         /* all-ASCII chunks (and the word before them) hold no error */
         if ((any & 0x80808080u) != 0 && first_err == NONE) {
+            gputf_u8state st = gputf_u8state_of(pw);
+            uint32_t errs[WORDS], anyerr = 0;
 #pragma unroll
-            for (int k = WORDS - 1; k >= 0; k--) {
-                uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors(k ? w[k - 1] : pw, w[k]));
-                if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
-                if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
+            for (int k = 0; k < WORDS; k++) {
+                errs[k] = gputf_utf8_errors_step(&st, w[k]);
+                anyerr |= errs[k];
+            }
+            if (anyerr) {   /* the first flagged byte of the chunk */
+#pragma unroll
+                for (int k = WORDS - 1; k >= 0; k--) {
+                    uint32_t nz = gputf_nonzero_bytes(errs[k]);
+                    if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
+                    if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
+                }
             }
         }
 #pragma unroll

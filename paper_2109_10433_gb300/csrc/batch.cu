@@ -597,6 +597,7 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
 {
     constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
     constexpr int HALO = 16;
+    static_assert(BPT % 4 == 0 && BPT <= 32, "whole words per thread, one flag bit per byte");
     const uint8_t *in = static_cast<const uint8_t *>(d.in);
     uint16_t *out = static_cast<uint16_t *>(d.out);
     const int tid = threadIdx.x;
@@ -623,6 +624,19 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
         s = sm.s_first + lo;
     }
 #define SIDX(x) ((long long)((x) - x0) + HALO)
+    /* error flags of the chunk's bytes, each checked against the three
+     * bytes before it whatever string they belong to (bit j: byte c0 + j);
+     * exact for every byte at least three past its string's start */
+    uint32_t fl = 0;
+    if (c0 < c1) {
+        const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage + SIDX(c0));
+        gputf_u8state u8s = gputf_u8state_of(sw[-1]);
+#pragma unroll
+        for (int k = 0; k < BPT / 4; k++) {
+            const uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors_step(&u8s, sw[k]));
+            fl |= ((((nz >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+        }
+    }
     /* phase A: units per byte, starts, first flagged byte per string */
     bool f = false;
     uint64_t v = 0;
@@ -643,7 +657,8 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
             v += len16_of(b);
             /* the flag sees the string's own bytes before i (the halo holds
              * the 7 before the tile) and zeros before the string's start */
-            if (flagged != ss && flag_at(stage, SIDX(i), SIDX(st), SIDX(en))) {
+            const bool fi = i - st < 3 ? flag_at(stage, SIDX(i), SIDX(st), SIDX(en)) : ((fl >> (i - c0)) & 1u) != 0;
+            if (flagged != ss && fi) {
                 record_string_error(d.errw, ss, epoch, i - st);
                 flagged = ss;
             }

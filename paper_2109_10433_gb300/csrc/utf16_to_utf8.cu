@@ -134,12 +134,22 @@ __device__ __forceinline__ void put_utf8(uint8_t *dst, uint32_t o, uint32_t u, u
 {
     const uint32_t c = (u << 10) + next - 0x35FDC00u;
     const uint32_t y = l == 4 ? c : u;
-    const uint32_t end = o + l;
+    const uint32_t sa = smem_u32(dst) + o;           /* shared-space address of the lead byte */
+    const uint32_t se = sa + l;                        /* one past the last byte */
     const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __funnelshift_r(0xF0E0C000u, 0u, 8 * l - 8);
-    if (l >= 1) dst[o] = (uint8_t)lead;
-    if (l >= 2) dst[end - 1] = (uint8_t)((y & 0x3F) | 0x80);
-    if (l >= 3) dst[end - 2] = (uint8_t)(((y >> 6) & 0x3F) | 0x80);
-    if (l == 4) dst[end - 3] = (uint8_t)(((y >> 12) & 0x3F) | 0x80);
+    const uint32_t b1 = (y & 0x3F) | 0x80, b2 = ((y >> 6) & 0x3F) | 0x80, b3 = ((y >> 12) & 0x3F) | 0x80;
+    /* predicated stores: lead at o, continuation bytes at end-1, end-2, end-3
+     * as far as the unit's length goes */
+    asm volatile("{\n\t.reg .pred p1, p2, p3, p4;\n\t"
+                 "setp.ne.u32 p1, %4, 0;\n\t"
+                 "setp.ge.u32 p2, %4, 2;\n\t"
+                 "setp.ge.u32 p3, %4, 3;\n\t"
+                 "setp.eq.u32 p4, %4, 4;\n\t"
+                 "@p1 st.shared.u8 [%0], %1;\n\t"
+                 "@p2 st.shared.u8 [%5+-1], %2;\n\t"
+                 "@p3 st.shared.u8 [%5+-2], %3;\n\t"
+                 "@p4 st.shared.u8 [%5+-3], %6;\n\t}"
+                 :: "r"(sa), "r"(lead), "r"(b1), "r"(b2), "r"(l), "r"(se), "r"(b3) : "memory");
 }
 
 constexpr int HALO16 = 8;   /* units staged on each side of a tile (16 bytes) */

@@ -592,12 +592,16 @@ def run_passes(args):
     cases = [
         ("utf16_to_utf8", "utf16", lambda: L.gputf_utf16_to_utf8(g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr,
                                                                  ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
+        ("utf16_to_utf8_unchecked", "utf16", lambda: L.gputf_utf16_to_utf8_unchecked(
+            g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr, ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
         ("validate_utf16", "utf16", lambda: L.gputf_validate_utf16(g._ptr(d16), n16, ws.ptr, ws.nbytes, g._ptr(res),
                                                                    sp), 2 * n16),
         ("utf8_length_from_utf16", "utf16", lambda: L.gputf_utf8_length_from_utf16(g._ptr(d16), n16, ws.ptr,
                                                                                    ws.nbytes, g._ptr(ln), sp), 2 * n16),
         ("utf8_to_utf16", "utf8", lambda: L.gputf_utf8_to_utf16(g._ptr(d8), n8, g._ptr(out16), n8, ws.ptr, ws.nbytes,
                                                                 g._ptr(res), sp), n8 + 2 * len16),
+        ("utf8_to_utf16_unchecked", "utf8", lambda: L.gputf_utf8_to_utf16_unchecked(
+            g._ptr(d8), n8, g._ptr(out16), n8, ws.ptr, ws.nbytes, g._ptr(res), sp), n8 + 2 * len16),
         ("validate_utf8", "utf8", lambda: L.gputf_validate_utf8(g._ptr(d8), n8, ws.ptr, ws.nbytes, g._ptr(res), sp),
          n8),
         ("utf16_length_from_utf8", "utf8", lambda: L.gputf_utf16_length_from_utf8(g._ptr(d8), n8, ws.ptr, ws.nbytes,
@@ -635,6 +639,81 @@ def run_passes(args):
     return 0
 
 
+def run_sweep(args):
+    """Throughput against input size: single calls of both transcoders on
+    sizes from 16 units to the whole buffer, and the batched call on many
+    strings of one size (up to 64 Ki units), each timed over back-to-back
+    launches with CUDA events.  UTF-16 input: the headline mix; UTF-8 input:
+    the 4-byte-heavy mix; cuts never split a character."""
+    import ctypes
+
+    import torch
+
+    import paper_2109_10433_gb300 as g
+    from paper_2109_10433_gb300 import batch as B
+
+    g.build()
+    torch.cuda.set_device(0)
+    L = g.lib()
+    s = torch.cuda.current_stream()
+    sp = g._stream(s)
+    u16 = W.cjk_emoji_utf16_256mib(nbytes=args.mib << 20)
+    u8 = W.utf8_text(2, 64 << 20, W.MIX_FOUR_BYTE_HEAVY)
+    d16 = torch.from_numpy(u16.view(np.int16).copy()).cuda()
+    d8 = torch.from_numpy(u8.copy()).cuda()
+    out8 = torch.empty(3 * u16.size, dtype=torch.uint8, device="cuda")
+    out16 = torch.empty(u8.size, dtype=torch.int16, device="cuda")
+    ws = g.Workspace(max(u16.size, u8.size) + 16)
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    is_high = (u16 & 0xFC00) == 0xD800
+    is_cont8 = (u8 & 0xC0) == 0x80
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    rows = []
+    sizes = [16 << (2 * k) for k in range(12)] + [u16.size]
+    for n in sizes:
+        n16 = min(n, u16.size)
+        if is_high[n16 - 1]:
+            n16 -= 1
+        reps = 200 if n16 < (1 << 20) else 20
+        us16 = timed(lambda: L.gputf_utf16_to_utf8(g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr, ws.nbytes,
+                                                   g._ptr(res), sp), reps)
+        row = {"units": n16, "utf16_to_utf8_us": us16, "utf16_to_utf8_input_gbs": 2 * n16 / us16 / 1e3}
+        n8 = min(n, u8.size)
+        while n8 < u8.size and is_cont8[n8]:
+            n8 -= 1
+        us8 = timed(lambda: L.gputf_utf8_to_utf16(g._ptr(d8), n8, g._ptr(out16), n8, ws.ptr, ws.nbytes,
+                                                  g._ptr(res), sp), reps)
+        row.update({"utf8_bytes": n8, "utf8_to_utf16_us": us8, "utf8_to_utf16_input_gbs": n8 / us8 / 1e3})
+        if n <= (64 << 10):
+            count = min(100000, (u16.size - 1) // n)
+            cuts = np.arange(count + 1, dtype=np.int64) * n
+            cuts[1:] -= is_high[cuts[1:] - 1]          # never split a pair
+            off = torch.from_numpy(cuts).cuda()
+            caps = torch.from_numpy(cuts * 3).cuda()
+            results = torch.zeros((count, 3), dtype=torch.int64, device="cuda")
+            cb = B.CBatch(count, int(cuts[-1]), d16.data_ptr(), off.data_ptr(), out8.data_ptr(), caps.data_ptr(),
+                          results.data_ptr())
+            bws = g.Workspace.of_bytes(int(L.gputf_batch_workspace_bytes(0, 0, int(cuts[-1]), count)))
+            usb = timed(lambda: L.gputf_batch_transcode(None, ctypes.byref(cb), 0, bws.ptr, bws.nbytes, sp), 20)
+            row.update({"batch_strings": count, "batch_us": usb, "batch_strings_per_s": count / (usb * 1e-6),
+                        "batch_input_gbs": 2 * int(cuts[-1]) / usb / 1e3})
+        rows.append(row)
+    print(json.dumps({"metric": "throughput vs input size (single calls and batched)", "sweep": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,7 +727,7 @@ def main():
     ap.add_argument("--mib", type=int, default=256,
                     help="input MiB of the UTF-16 workload (256 is the measured configuration; "
                          "smaller sizes are for profiler captures)")
-    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve", "passes"])
+    ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve", "passes", "sweep"])
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--budget-gb", type=int, default=8)
     ap.add_argument("--slots", type=int, default=4)
@@ -663,6 +742,8 @@ def main():
         return run_serve(args)
     if args.workload == "passes" and args.impl != "reference":
         return run_passes(args)
+    if args.workload == "sweep" and args.impl != "reference":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

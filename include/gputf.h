@@ -118,6 +118,17 @@ gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *ou
 gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
 
+/* Transcoding without validation (the paper's non-validating transcoders,
+ * Table 4): the caller vouches that the input is valid.  Same arguments,
+ * workspace and capacity rules as the validating calls; on valid input the
+ * result and output are identical to theirs.  On invalid input nothing is
+ * checked: res->error is GPUTF_OK or GPUTF_OUTPUT_TOO_SMALL, the output is
+ * unspecified, and still nothing is written past out_cap. */
+gputf_status gputf_utf8_to_utf16_unchecked(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
+                                           void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+gputf_status gputf_utf16_to_utf8_unchecked(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
+                                           void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+
 /* Validation only (Section 3, UTF-8 rules 1-6): res->error and res->position
  * as for gputf_utf8_to_utf16, res->written = 0. */
 gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,

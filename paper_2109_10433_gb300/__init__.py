@@ -46,6 +46,8 @@ SIGNATURES = {
     "gputf_workspace_init": ([_P, _S, _P], _I),
     "gputf_utf8_to_utf16": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
     "gputf_utf16_to_utf8": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf8_to_utf16_unchecked": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf16_to_utf8_unchecked": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
     "gputf_validate_utf8": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_validate_utf16": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf16_length_from_utf8": ([_P, _S, _P, _S, _P, _P], _I),
@@ -189,32 +191,35 @@ def _ws_for(ws, n):
     return ws
 
 
-def utf8_to_utf16(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True):
+def utf8_to_utf16(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True,
+                  validate: bool = True):
     """UTF-8 bytes (CUDA uint8 tensor) -> UTF-16LE units.  Returns
     (Result, out) when sync, else (res tensor, out); `out` defaults to n units
-    (torch.int16 storage)."""
+    (torch.int16 storage).  validate=False calls the non-validating form."""
     torch = _torch()
     n = inp.numel() * inp.element_size()
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=inp.device)
     cap = out.numel() * out.element_size() // 2
     ws, res = _ws_for(ws, n), _res_tensor(res)
-    _check(lib().gputf_utf8_to_utf16(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes,
-                                     _ptr(res), _stream(stream)), "gputf_utf8_to_utf16")
+    name = "gputf_utf8_to_utf16" if validate else "gputf_utf8_to_utf16_unchecked"
+    _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
 
-def utf16_to_utf8(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True):
+def utf16_to_utf8(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True,
+                  validate: bool = True):
     """UTF-16LE units (CUDA tensor of 2-byte elements) -> UTF-8 bytes.
-    `out` defaults to 3 bytes per unit (torch.uint8)."""
+    `out` defaults to 3 bytes per unit (torch.uint8).  validate=False calls
+    the non-validating form."""
     torch = _torch()
     n = inp.numel() * inp.element_size() // 2
     if out is None:
         out = torch.empty(max(3 * n, 1), dtype=torch.uint8, device=inp.device)
     cap = out.numel() * out.element_size()
     ws, res = _ws_for(ws, n), _res_tensor(res)
-    _check(lib().gputf_utf16_to_utf8(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes,
-                                     _ptr(res), _stream(stream)), "gputf_utf16_to_utf8")
+    name = "gputf_utf16_to_utf8" if validate else "gputf_utf16_to_utf8_unchecked"
+    _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
 

@@ -93,6 +93,38 @@ cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s)
 }
 }  // namespace gputf
 
+namespace {
+gputf_status utf8_to_utf16_call(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap, void *ws,
+                                size_t ws_bytes, gputf_result *res, bool validate, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    if ((out_cap > 0 && out == nullptr) || !aligned(out, 2)) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (gputf::utf8_to_utf16_tiles(in, n_bytes) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
+                                                   reinterpret_cast<gputf::DevResult *>(res), sms, validate,
+                                                   stream));
+}
+
+gputf_status utf16_to_utf8_call(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap, void *ws,
+                                size_t ws_bytes, gputf_result *res, bool validate, cudaStream_t stream)
+{
+    uint64_t words;
+    gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
+    if (st != GPUTF_STATUS_OK) return st;
+    if (out_cap > 0 && out == nullptr) return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (gputf::utf16_to_utf8_tiles(in, n_units) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
+    int sms;
+    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
+    return cuda_status(gputf::launch_utf16_to_utf8(in, n_units, out, out_cap, ws, words,
+                                                   reinterpret_cast<gputf::DevResult *>(res), sms, validate,
+                                                   stream));
+}
+}  // namespace
+
 extern "C" {
 
 size_t gputf_workspace_bytes(size_t max_units)
@@ -112,32 +144,29 @@ gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream
     return cuda_status(gputf::launch_workspace_init(ws, ws_bytes, stream));
 }
 
+
 gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    uint64_t words;
-    gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
-    if (st != GPUTF_STATUS_OK) return st;
-    if ((out_cap > 0 && out == nullptr) || !aligned(out, 2)) return GPUTF_STATUS_INVALID_ARGUMENT;
-    if (gputf::utf8_to_utf16_tiles(in, n_bytes) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
-    int sms;
-    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
-    return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
-                                                   reinterpret_cast<gputf::DevResult *>(res), sms, stream));
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, stream);
 }
 
 gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    uint64_t words;
-    gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
-    if (st != GPUTF_STATUS_OK) return st;
-    if (out_cap > 0 && out == nullptr) return GPUTF_STATUS_INVALID_ARGUMENT;
-    if (gputf::utf16_to_utf8_tiles(in, n_units) > words) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
-    int sms;
-    if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
-    return cuda_status(gputf::launch_utf16_to_utf8(in, n_units, out, out_cap, ws, words,
-                                                   reinterpret_cast<gputf::DevResult *>(res), sms, stream));
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, stream);
+}
+
+gputf_status gputf_utf8_to_utf16_unchecked(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
+                                           void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, false, stream);
+}
+
+gputf_status gputf_utf16_to_utf8_unchecked(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
+                                           void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, false, stream);
 }
 
 gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,

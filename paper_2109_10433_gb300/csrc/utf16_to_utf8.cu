@@ -186,7 +186,7 @@ struct U16Layout {
  * mbarriers.  Tiles at the ends of the buffer (halo outside the input) are
  * filled by the threads with guarded loads instead.
  */
-template <int THREADS, int UPT, int STAGES>
+template <int THREADS, int UPT, int STAGES, bool VALIDATE>
 __global__ void __launch_bounds__(THREADS)
 utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
@@ -286,27 +286,45 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
             /* bytes per unit, two units per step (Table 2, with a surrogate
-             * pair written whole by its high unit): 1 + [u >= 0x80] +
-             * [u >= 0x800] + [high] - 3 [low], i.e. 4 for a high unit, 0 for
-             * a low one and len8 for the rest; and Section 3's pairing rule
-             * read as "the unit before is high" == "this unit is low" for
-             * every two adjacent units */
+             * pair written whole by its high unit): len8 (1, 2 or 3; 2 for a
+             * surrogate), plus 2 for a high unit followed by a low one, minus
+             * 2 for a low unit that follows a high one, so a pair gives 4 + 0
+             * and a lone surrogate 2: no tile needs more than 3 bytes a unit
+             * (plus one for a pair cut by the tile's end).  A word's "next
+             * unit is low" flags need the next word, so each word is
+             * finished one step later.  Section 3's pairing rule is checked
+             * as "the unit before is high" == "this unit is low" for every
+             * two adjacent units. */
             uint32_t lanes = 0, bad = 0, hcarry = is_high(pu) ? 0x8000u : 0u;
+            uint32_t p_base = 0, p_hi = 0, p_lo = 0, p_ph = 0;   /* the word before */
 #pragma unroll
-            for (int k = 0; k < WORDS; k++) {
-                const uint32_t x = w[k];
-                const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-                const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-                const uint32_t sg = (x & 0xFC00FC00u) ^ 0xD800D800u;
-                const uint32_t hi = zero_halves(sg), lo = zero_halves(sg ^ 0x04000400u);
-                /* per-half byte counts (0..4) in bits 0-2 and 16-18 */
-                const uint32_t L = 0x00010001u + (ge80 >> 15) + (ge800 >> 15) + (hi >> 15) - 3u * (lo >> 15);
-                lanes += L;
-                n_nib[k / 4] |= ((L | (L >> 12)) & 0xFFu) << (8 * (k % 4));
-                bad |= ((hi << 16) | hcarry) ^ lo;   /* bit 15: pair (2k-1, 2k); bit 31: (2k, 2k+1) */
-                hcarry = hi >> 16;
+            for (int k = 0; k <= WORDS; k++) {
+                uint32_t base = 0, hi = 0, lo = is_low(nu) ? 0x8000u : 0u, ph = 0;
+                if (k < WORDS) {
+                    const uint32_t x = w[k];
+                    const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+                    const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
+                    const uint32_t sg = (x & 0xFC00FC00u) ^ 0xD800D800u;
+                    hi = zero_halves(sg);
+                    lo = zero_halves(sg ^ 0x04000400u);
+                    /* len8 per half (0..3) in bits 0-1 and 16-17 */
+                    base = 0x00010001u + (ge80 >> 15) + (ge800 >> 15) - ((hi | lo) >> 15);
+                    ph = (hi << 16) | hcarry;   /* bit 15: unit 2k-1 is high; bit 31: unit 2k is high */
+                    if (VALIDATE) bad |= ph ^ lo;
+                    hcarry = hi >> 16;
+                }
+                if (k > 0) {   /* finish word k-1 */
+                    const uint32_t nl = __funnelshift_r(p_lo, lo, 16);   /* its units' next unit is low */
+                    const uint32_t L = p_base + ((p_hi & nl) >> 14) - ((p_lo & p_ph) >> 14);
+                    lanes += L;
+                    n_nib[(k - 1) / 4] |= ((L | (L >> 12)) & 0xFFu) << (8 * ((k - 1) % 4));
+                }
+                p_base = base;
+                p_hi = hi;
+                p_lo = lo;
+                p_ph = ph;
             }
-            bad |= (uint32_t)((hcarry != 0) != is_low(nu));
+            if (VALIDATE) bad |= (uint32_t)((hcarry != 0) != is_low(nu));
             n_total = (lanes & 0xFFFF) + (lanes >> 16);
             uint32_t inr = 0xFFFFFFFFu;
             if (!interior) {   /* units outside the input write nothing */
@@ -322,7 +340,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 }
             }
             uint64_t first_err = NONE;
-            if (bad) {   /* some pair breaks the rule: find the first invalid unit of the chunk */
+            if (VALIDATE && bad) {   /* some pair breaks the rule: find the first invalid unit of the chunk */
                 uint32_t prev = pu;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
@@ -486,15 +504,18 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         written = ld_relaxed(status + tiles - 1) & VALUE_MASK;
     } else if (error != GPUTF_E_TIMEOUT) {
         /* bytes of [0, pos): the tiles before pos's tile, then a recount
-         * with the same per-unit convention (every pair in it is complete:
-         * pos is the first error or the start of a character) */
+         * with the kernel's per-unit convention (a pair's 4 bytes on its high
+         * unit, 2 for a lone surrogate, which only the non-validating call
+         * can meet before pos) */
         const uint64_t t = (head + pos) / TILE;
         const uint64_t before = t ? (ld_relaxed(status + t - 1) & VALUE_MASK) : 0;
         const uint64_t start = t * TILE > head ? t * TILE - head : 0;
         uint32_t c = 0;
         for (uint64_t i = start + tid; i < pos; i += THREADS) {
             const uint32_t u = in[i];
-            c += (is_low(u) && i > 0 && is_high(in[i - 1])) ? 0u : (is_high(u) ? 4u : len8(u));
+            if (is_high(u)) c += (i + 1 < n && is_low(in[i + 1])) ? 4u : 2u;
+            else if (is_low(u)) c += (i > 0 && is_high(in[i - 1])) ? 0u : 2u;
+            else c += len8(u);
         }
         uint32_t sum;
         block_exclusive<THREADS>(c, s_warp, &sum);
@@ -661,11 +682,11 @@ uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
     return (((uintptr_t)in % 16) / 2 + n + U16Lay::TILE) / U16Lay::TILE;   /* at least one tile */
 }
 
-cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
-                                 void *ws, uint64_t status_words, DevResult *res, int sms,
-                                 cudaStream_t stream)
+template <bool VALIDATE>
+static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap, void *ws,
+                            uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES>;
+    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE>;
     static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U16Lay::SMEM);
@@ -681,6 +702,14 @@ cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, u
     kern<<<(unsigned)grid, U16_THREADS, U16Lay::SMEM, stream>>>(in, n, out, cap, hdr, status,
                                                                  status_words, tiles, res);
     return cudaGetLastError();
+}
+
+cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
+                                 cudaStream_t stream)
+{
+    return validate ? launch16<true>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch16<false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

@@ -133,7 +133,7 @@ struct U8Layout {
  * side: the 3 bytes before a position validate it, the 3 after complete a
  * character that starts near the tile's end.
  */
-template <int THREADS, int WORDS, int STAGES>
+template <int THREADS, int WORDS, int STAGES, bool VALIDATE>
 __global__ void __launch_bounds__(THREADS)
 utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
@@ -238,7 +238,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             /* validation, skipped by all-ASCII warps and all-ASCII threads */
             const bool ascii = (any & 0x80808080u) == 0;
             uint64_t first_err = NONE;
-            if (!__all_sync(FULL_MASK, ascii) && !ascii) {
+            if (VALIDATE && !__all_sync(FULL_MASK, ascii) && !ascii) {
                 gputf_u8state st = gputf_u8state_of(pw);
                 uint32_t errs[WORDS], anyerr = 0;
 #pragma unroll
@@ -609,11 +609,11 @@ uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
     return ((uintptr_t)in % 16 + n + 1 + U8Lay::TILE - 1) / U8Lay::TILE;
 }
 
-cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
-                                 void *ws, uint64_t status_words, DevResult *res, int sms,
-                                 cudaStream_t stream)
+template <bool VALIDATE>
+static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap, void *ws,
+                           uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES>;
+    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE>;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U8Lay::SMEM);
@@ -629,6 +629,14 @@ cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, u
     kern<<<(unsigned)grid, U8_THREADS, U8Lay::SMEM, stream>>>(in, n, out, cap, hdr, status, status_words,
                                                               tiles, res);
     return cudaGetLastError();
+}
+
+cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
+                                 void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
+                                 cudaStream_t stream)
+{
+    return validate ? launch8<true>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch8<false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

@@ -316,3 +316,73 @@ def test_validate_utf16_one_error_anywhere_in_a_long_buffer(g, ws):
             inp = dev_u16(d, p % 8)
             assert tuple(g.validate_utf16(inp, ws=ws)) == tuple(oracle.validate_utf16(d)), (form, p)
             assert g.utf8_length_from_utf16(inp, ws=ws) == oracle.utf8_length_from_utf16(d), (form, p)
+
+
+def test_unchecked_equals_checked_on_valid_input(g, ws):
+    """The non-validating calls give the validating calls' result and output
+    on valid input: every mix, sizes across tiles and alignments, and the
+    256 MiB benchmark buffer."""
+    for i, mix in enumerate(MIXES):
+        for n in (1, 37, TILE8 - 1, 3 * TILE8 + 17):
+            d8 = W.utf8_text(50 + i, n, mix)
+            a, oa = g.utf8_to_utf16(dev_u8(d8, i % 16), ws=ws)
+            b, ob = g.utf8_to_utf16(dev_u8(d8, i % 16), ws=ws, validate=False)
+            assert tuple(a) == tuple(b) and a.error == 0
+            assert torch.equal(oa[:a.written], ob[:b.written])
+        for n in (1, 37, TILE16 - 1, 3 * TILE16 + 17):
+            d16 = W.utf16_text(60 + i, n, mix)
+            a, oa = g.utf16_to_utf8(dev_u16(d16, i % 8), ws=ws)
+            b, ob = g.utf16_to_utf8(dev_u16(d16, i % 8), ws=ws, validate=False)
+            assert tuple(a) == tuple(b) and a.error == 0
+            assert torch.equal(oa[:a.written], ob[:b.written])
+    d = W.cjk_emoji_utf16_256mib()
+    inp = dev_u16(d)
+    a, oa = g.utf16_to_utf8(inp, ws=ws)
+    b, ob = g.utf16_to_utf8(inp, ws=ws, validate=False)
+    assert tuple(a) == tuple(b) and torch.equal(oa[:a.written], ob[:b.written])
+
+
+def test_unchecked_on_invalid_input_stays_in_bounds(g, ws):
+    """Without validation, invalid input gives OK or OUTPUT_TOO_SMALL and an
+    unspecified output, but nothing outside the output buffer is touched,
+    also with capacities that cut the output short."""
+    rng = np.random.default_rng(23)
+    for trial in range(40):
+        n = int(rng.integers(1, 3 * TILE8))
+        b = rng.integers(0, 256, n).astype(np.uint8)
+        cap = int(rng.integers(0, 2 * n + 4)) if trial % 3 == 0 else n
+        outbuf = torch.full((cap + 32,), GUARD * 257, dtype=torch.int16, device="cuda")
+        r, _ = g.utf8_to_utf16(dev_u8(b, trial % 16), out=outbuf[8:8 + cap], ws=ws, validate=False)
+        assert r.error in (oracle.OK, oracle.OUTPUT_TOO_SMALL) and r.written <= cap
+        host = outbuf.cpu().numpy().view(np.uint16)
+        assert np.all(host[:8] == GUARD * 257) and np.all(host[8 + cap:] == GUARD * 257)
+        u = rng.integers(0, 65536, n).astype(np.uint16)
+        u[rng.random(n) < 0.3] = rng.integers(0xD800, 0xE000, int((rng.random(n) < 0.3).sum()) or 1)[0]
+        cap = int(rng.integers(0, 3 * n + 4)) if trial % 3 == 0 else 3 * n
+        outbuf = torch.full((cap + 64,), GUARD, dtype=torch.uint8, device="cuda")
+        r, _ = g.utf16_to_utf8(dev_u16(u, trial % 8), out=outbuf[16:16 + cap], ws=ws, validate=False)
+        assert r.error in (oracle.OK, oracle.OUTPUT_TOO_SMALL) and r.written <= cap
+        host = outbuf.cpu().numpy()
+        assert np.all(host[:16] == GUARD) and np.all(host[16 + cap:] == GUARD)
+
+
+def test_dense_lone_surrogates_fit_the_staging_buffer(g, ws):
+    """Input made of lone or mis-ordered surrogates over several tiles: a
+    lone surrogate counts 2 bytes, so no tile's output outgrows the staging
+    buffer.  The validating call reports the oracle's first error; the
+    non-validating call stays inside the output buffer."""
+    rng = np.random.default_rng(29)
+    n = 3 * TILE16 + 5
+    cases = [np.full(n, 0xD800, np.uint16), np.full(n, 0xDFFF, np.uint16),
+             np.tile(np.array([0xDC00, 0xD800], np.uint16), n // 2),
+             rng.integers(0xD800, 0xE000, n).astype(np.uint16),
+             np.where(rng.random(n) < 0.5, 0xDBFF, 0x9FFF).astype(np.uint16)]
+    for u in cases:
+        check_16to8(g, ws, u)
+        check_passes16(g, ws, u)
+        for cap in (3 * u.size, u.size):
+            outbuf = torch.full((cap + 64,), GUARD, dtype=torch.uint8, device="cuda")
+            r, _ = g.utf16_to_utf8(dev_u16(u), out=outbuf[16:16 + cap], ws=ws, validate=False)
+            assert r.error in (oracle.OK, oracle.OUTPUT_TOO_SMALL) and r.written <= cap
+            host = outbuf.cpu().numpy()
+            assert np.all(host[:16] == GUARD) and np.all(host[16 + cap:] == GUARD)

@@ -581,6 +581,9 @@ def run_passes(args):
     d16 = torch.from_numpy(u16.view(np.int16).copy()).cuda()
     d8 = torch.from_numpy(u8.copy()).cuda()
     n16, n8 = int(u16.size), int(u8.size)
+    # script-uniform UTF-16 text of the same size: all U+4E00-9FFF, all ASCII
+    cjk = torch.from_numpy(W.utf16_text(5, n16, W.SCRIPT_CJK).view(np.int16).copy()).cuda()
+    asc = torch.from_numpy(W.utf16_text(6, n16, W.SCRIPT_ASCII).view(np.int16).copy()).cuda()
     out8 = torch.empty(3 * n16, dtype=torch.uint8, device="cuda")
     out16 = torch.empty(n8, dtype=torch.int16, device="cuda")
     ws = g.Workspace(max(n16, n8) + 16)
@@ -594,6 +597,10 @@ def run_passes(args):
                                                                  ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
         ("utf16_to_utf8_unchecked", "utf16", lambda: L.gputf_utf16_to_utf8_unchecked(
             g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr, ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
+        ("utf16_to_utf8 cjk-only", "utf16", lambda: L.gputf_utf16_to_utf8(
+            g._ptr(cjk), n16, g._ptr(out8), 3 * n16, ws.ptr, ws.nbytes, g._ptr(res), sp), 2 * n16 + 3 * n16),
+        ("utf16_to_utf8 ascii-only", "utf16", lambda: L.gputf_utf16_to_utf8(
+            g._ptr(asc), n16, g._ptr(out8), 3 * n16, ws.ptr, ws.nbytes, g._ptr(res), sp), 2 * n16 + n16),
         ("validate_utf16", "utf16", lambda: L.gputf_validate_utf16(g._ptr(d16), n16, ws.ptr, ws.nbytes, g._ptr(res),
                                                                    sp), 2 * n16),
         ("utf8_length_from_utf16", "utf16", lambda: L.gputf_utf8_length_from_utf16(g._ptr(d16), n16, ws.ptr,

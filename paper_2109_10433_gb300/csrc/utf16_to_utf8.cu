@@ -376,13 +376,44 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 w[4 * v + 3] = q.w;
             }
             const uint32_t nu = sb[i0 + UPT];
-            /* each unit's bytes, at offsets from the tile's first output byte */
-            uint32_t o = c_excl;
+            /* each unit's bytes, at offsets from the tile's first output byte.
+             * Uniform-class fast paths: when every unit of every thread of
+             * the warp takes 3 bytes (BMP from U+0800, no surrogate), or 1,
+             * or 2, the bytes go to fixed offsets with no per-unit length
+             * work (the same bytes the general path writes). */
+            uint32_t nib_and = c_nib[0], nib_or = c_nib[0];
 #pragma unroll
-            for (int k = 0; k < UPT; k++) {
-                const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
-                put_utf8(outb, o, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
-                o += l;
+            for (int j = 1; j < NW; j++) {
+                nib_and &= c_nib[j];
+                nib_or |= c_nib[j];
+            }
+            uint8_t *dst = outb + c_excl;
+            if (__all_sync(FULL_MASK, nib_and == 0x33333333u && nib_or == 0x33333333u)) {
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    dst[3 * k] = (uint8_t)(0xE0 | (u >> 12));
+                    dst[3 * k + 1] = (uint8_t)(0x80 | ((u >> 6) & 0x3F));
+                    dst[3 * k + 2] = (uint8_t)(0x80 | (u & 0x3F));
+                }
+            } else if (__all_sync(FULL_MASK, nib_and == 0x11111111u && nib_or == 0x11111111u)) {
+#pragma unroll
+                for (int k = 0; k < UPT; k++) dst[k] = (uint8_t)UNIT(k);
+            } else if (__all_sync(FULL_MASK, nib_and == 0x22222222u && nib_or == 0x22222222u)) {
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    dst[2 * k] = (uint8_t)(0xC0 | (u >> 6));
+                    dst[2 * k + 1] = (uint8_t)(0x80 | (u & 0x3F));
+                }
+            } else {
+                uint32_t o = c_excl;
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
+                    put_utf8(outb, o, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
+                    o += l;
+                }
             }
 
             /* the window: usable when an inclusive prefix appears in it and

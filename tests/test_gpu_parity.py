@@ -386,3 +386,24 @@ def test_dense_lone_surrogates_fit_the_staging_buffer(g, ws):
             assert r.error in (oracle.OK, oracle.OUTPUT_TOO_SMALL) and r.written <= cap
             host = outbuf.cpu().numpy()
             assert np.all(host[:16] == GUARD) and np.all(host[16 + cap:] == GUARD)
+
+
+def test_uniform_and_mixed_warps_in_one_tile(g, ws):
+    """Runs of one script (all 3-byte, all ASCII, all 2-byte, 2-byte with lone
+    surrogates) next to mixed text, with run lengths that are not multiples
+    of a warp's 768 units: warps on the uniform-class fast paths and warps on
+    the general path share tiles and write adjacent bytes."""
+    rng = np.random.default_rng(31)
+    scripts = [W.SCRIPT_CJK, W.SCRIPT_ASCII, W.SCRIPT_TWO_BYTE, W.MIX_CJK_EMOJI]
+    for trial in range(12):
+        parts = []
+        for p in range(int(rng.integers(3, 9))):
+            n = int(rng.integers(1, 4000)) if p % 2 else int(rng.integers(700, 6000))
+            parts.append(W.utf16_text(1000 + 10 * trial + p, n, scripts[int(rng.integers(0, 4))]))
+        d = np.concatenate(parts).astype(np.uint16)
+        check_16to8(g, ws, d, in_off=trial % 8, out_off=trial % 16)
+    # a 2-byte run with lone surrogates in it: the error is reported, the prefix exact
+    d = W.utf16_text(77, 5000, W.SCRIPT_TWO_BYTE).copy()
+    d[3001] = 0xD800
+    check_16to8(g, ws, d)
+    check_16to8(g, ws, d, cap=2500)

@@ -282,7 +282,6 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                 w[4 * v + 2] = q.z;
                 w[4 * v + 3] = q.w;
             }
-            const uint32_t nw = *reinterpret_cast<const uint32_t *>(sb + i0 + BPT);
             uint32_t lead[WORDS], any = 0;
 #pragma unroll
             for (int k = 0; k < WORDS; k++) {

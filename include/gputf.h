@@ -150,6 +150,22 @@ gputf_status gputf_utf16_length_from_utf8(const uint8_t *in, size_t n_bytes, voi
 gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, void *ws,
                                           size_t ws_bytes, uint64_t *len, cudaStream_t stream);
 
+/* Big-endian UTF-16 (UTF-16BE).  The paper treats UTF-16LE only (Section 3:
+ * the byte order of the host); these are the same four operations on 16-bit
+ * units stored most significant byte first, with the same arguments,
+ * workspace, capacity and result rules as the UTF-16LE calls above.  Each
+ * gives what the UTF-16LE call gives on the byte-swapped units (and, for
+ * gputf_utf8_to_utf16be, writes the byte-swapped units).  `in` and `out` are
+ * still 2-byte aligned arrays of 16-bit units. */
+gputf_status gputf_utf16be_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
+                                   void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+gputf_status gputf_utf8_to_utf16be(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
+                                   void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream);
+gputf_status gputf_validate_utf16be(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                    gputf_result *res, cudaStream_t stream);
+gputf_status gputf_utf8_length_from_utf16be(const uint16_t *in, size_t n_units, void *ws,
+                                            size_t ws_bytes, uint64_t *len, cudaStream_t stream);
+
 /* Host-buffer forms of the two transcoders, for callers whose text lives in
  * host memory: copies `h_in` to the device buffer `d_in`, transcodes into
  * `d_out`, copies the result struct to `h_res` and the `written` output units

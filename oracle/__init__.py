@@ -164,6 +164,32 @@ def utf8_length_from_utf16(units) -> int:
     return int(_load().oracle_utf8_length_from_utf16(_ptr(a), a.size))
 
 
+# UTF-16BE.  The paper's UTF-16 is little-endian (Section 3); big-endian
+# UTF-16 stores the same 16-bit units with their two bytes exchanged.  The
+# oracle therefore swaps the bytes of each unit and applies the UTF-16LE
+# definitions above (and swaps the units it writes).
+
+def _swap16(a: np.ndarray) -> np.ndarray:
+    return a.byteswap()
+
+
+def utf16be_to_utf8(units, cap: int | None = None):
+    return utf16_to_utf8(_swap16(_u16(units)), cap)
+
+
+def utf8_to_utf16be(data, cap: int | None = None):
+    res, out = utf8_to_utf16(data, cap)
+    return res, _swap16(out)
+
+
+def validate_utf16be(units) -> Result:
+    return validate_utf16(_swap16(_u16(units)))
+
+
+def utf8_length_from_utf16be(units) -> int:
+    return utf8_length_from_utf16(_swap16(_u16(units)))
+
+
 def encode_utf8(cp: int) -> bytes:
     buf = (ctypes.c_uint8 * 4)()
     k = _load().oracle_encode_utf8(cp, buf)

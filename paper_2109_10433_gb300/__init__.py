@@ -52,6 +52,10 @@ SIGNATURES = {
     "gputf_validate_utf16": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf16_length_from_utf8": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf8_length_from_utf16": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf16be_to_utf8": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf8_to_utf16be": ([_P, _S, _P, _S, _P, _S, _P, _P], _I),
+    "gputf_validate_utf16be": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_utf8_length_from_utf16be": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf8_to_utf16_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_static": ([_P, _S, _P, _S, _P, _P], _I),
@@ -191,34 +195,43 @@ def _ws_for(ws, n):
     return ws
 
 
+def _utf16_name(base, validate, big_endian):
+    if big_endian and not validate:
+        raise ValueError("the non-validating transcoders take UTF-16LE only")
+    if big_endian:
+        return base.replace("utf16", "utf16be")
+    return base if validate else base + "_unchecked"
+
+
 def utf8_to_utf16(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True,
-                  validate: bool = True):
-    """UTF-8 bytes (CUDA uint8 tensor) -> UTF-16LE units.  Returns
-    (Result, out) when sync, else (res tensor, out); `out` defaults to n units
-    (torch.int16 storage).  validate=False calls the non-validating form."""
+                  validate: bool = True, big_endian: bool = False):
+    """UTF-8 bytes (CUDA uint8 tensor) -> UTF-16LE units (UTF-16BE when
+    big_endian).  Returns (Result, out) when sync, else (res tensor, out);
+    `out` defaults to n units (torch.int16 storage).  validate=False calls the
+    non-validating form."""
     torch = _torch()
     n = inp.numel() * inp.element_size()
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=inp.device)
     cap = out.numel() * out.element_size() // 2
+    name = _utf16_name("gputf_utf8_to_utf16", validate, big_endian)
     ws, res = _ws_for(ws, n), _res_tensor(res)
-    name = "gputf_utf8_to_utf16" if validate else "gputf_utf8_to_utf16_unchecked"
     _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
 
 def utf16_to_utf8(inp, out=None, ws: Workspace | None = None, res=None, stream=None, sync=True,
-                  validate: bool = True):
-    """UTF-16LE units (CUDA tensor of 2-byte elements) -> UTF-8 bytes.
-    `out` defaults to 3 bytes per unit (torch.uint8).  validate=False calls
-    the non-validating form."""
+                  validate: bool = True, big_endian: bool = False):
+    """UTF-16LE units (UTF-16BE when big_endian; CUDA tensor of 2-byte
+    elements) -> UTF-8 bytes.  `out` defaults to 3 bytes per unit
+    (torch.uint8).  validate=False calls the non-validating form."""
     torch = _torch()
     n = inp.numel() * inp.element_size() // 2
     if out is None:
         out = torch.empty(max(3 * n, 1), dtype=torch.uint8, device=inp.device)
     cap = out.numel() * out.element_size()
+    name = _utf16_name("gputf_utf16_to_utf8", validate, big_endian)
     ws, res = _ws_for(ws, n), _res_tensor(res)
-    name = "gputf_utf16_to_utf8" if validate else "gputf_utf16_to_utf8_unchecked"
     _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
@@ -231,11 +244,11 @@ def validate_utf8(inp, ws: Workspace | None = None, res=None, stream=None, sync=
     return read_result(res) if sync else res
 
 
-def validate_utf16(inp, ws: Workspace | None = None, res=None, stream=None, sync=True):
+def validate_utf16(inp, ws: Workspace | None = None, res=None, stream=None, sync=True, big_endian: bool = False):
     n = inp.numel() * inp.element_size() // 2
     ws, res = _ws_for(ws, n), _res_tensor(res)
-    _check(lib().gputf_validate_utf16(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)),
-           "gputf_validate_utf16")
+    name = "gputf_validate_utf16be" if big_endian else "gputf_validate_utf16"
+    _check(getattr(lib(), name)(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return read_result(res) if sync else res
 
 
@@ -252,11 +265,12 @@ def utf16_length_from_utf8(inp, ws: Workspace | None = None, out=None, stream=No
     return int(out.item()) if sync else out
 
 
-def utf8_length_from_utf16(inp, ws: Workspace | None = None, out=None, stream=None, sync=True):
+def utf8_length_from_utf16(inp, ws: Workspace | None = None, out=None, stream=None, sync=True,
+                           big_endian: bool = False):
     n = inp.numel() * inp.element_size() // 2
     ws, out = _ws_for(ws, n), _len_tensor(out)
-    _check(lib().gputf_utf8_length_from_utf16(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out),
-                                              _stream(stream)), "gputf_utf8_length_from_utf16")
+    name = "gputf_utf8_length_from_utf16be" if big_endian else "gputf_utf8_length_from_utf16"
+    _check(getattr(lib(), name)(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out), _stream(stream)), name)
     return int(out.item()) if sync else out
 
 

@@ -95,7 +95,8 @@ cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s)
 
 namespace {
 gputf_status utf8_to_utf16_call(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap, void *ws,
-                                size_t ws_bytes, gputf_result *res, bool validate, cudaStream_t stream)
+                                size_t ws_bytes, gputf_result *res, bool validate, bool big_endian,
+                                cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
@@ -106,11 +107,12 @@ gputf_status utf8_to_utf16_call(const uint8_t *in, size_t n_bytes, uint16_t *out
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
                                                    reinterpret_cast<gputf::DevResult *>(res), sms, validate,
-                                                   stream));
+                                                   big_endian, stream));
 }
 
 gputf_status utf16_to_utf8_call(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap, void *ws,
-                                size_t ws_bytes, gputf_result *res, bool validate, cudaStream_t stream)
+                                size_t ws_bytes, gputf_result *res, bool validate, bool big_endian,
+                                cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
@@ -121,7 +123,7 @@ gputf_status utf16_to_utf8_call(const uint16_t *in, size_t n_units, uint8_t *out
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf16_to_utf8(in, n_units, out, out_cap, ws, words,
                                                    reinterpret_cast<gputf::DevResult *>(res), sms, validate,
-                                                   stream));
+                                                   big_endian, stream));
 }
 }  // namespace
 
@@ -148,25 +150,25 @@ gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream
 gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, stream);
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, false, stream);
 }
 
 gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, stream);
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, false, stream);
 }
 
 gputf_status gputf_utf8_to_utf16_unchecked(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
                                            void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, false, stream);
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, false, false, stream);
 }
 
 gputf_status gputf_utf16_to_utf8_unchecked(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                            void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, false, stream);
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, false, false, stream);
 }
 
 gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,
@@ -181,16 +183,22 @@ gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, si
                                                    reinterpret_cast<gputf::DevResult *>(res), sms, stream));
 }
 
-gputf_status gputf_validate_utf16(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
-                                  gputf_result *res, cudaStream_t stream)
+static gputf_status validate_utf16_call(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                       gputf_result *res, bool big_endian, cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
     if (st != GPUTF_STATUS_OK) return st;
     int sms;
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
-    return cuda_status(gputf::launch_validate_utf16(in, n_units, ws,
-                                                    reinterpret_cast<gputf::DevResult *>(res), sms, stream));
+    return cuda_status(gputf::launch_validate_utf16(in, n_units, ws, reinterpret_cast<gputf::DevResult *>(res),
+                                                    sms, big_endian, stream));
+}
+
+gputf_status gputf_validate_utf16(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                  gputf_result *res, cudaStream_t stream)
+{
+    return validate_utf16_call(in, n_units, ws, ws_bytes, res, false, stream);
 }
 
 gputf_status gputf_utf16_length_from_utf8(const uint8_t *in, size_t n_bytes, void *ws,
@@ -205,8 +213,8 @@ gputf_status gputf_utf16_length_from_utf8(const uint8_t *in, size_t n_bytes, voi
         in, n_bytes, ws, reinterpret_cast<unsigned long long *>(len), sms, stream));
 }
 
-gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, void *ws,
-                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream)
+static gputf_status utf8_length_from_utf16_call(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                                uint64_t *len, bool big_endian, cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_units, ws, ws_bytes, len, 2, &words);
@@ -214,7 +222,37 @@ gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, vo
     int sms;
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf8_length_from_utf16(
-        in, n_units, ws, reinterpret_cast<unsigned long long *>(len), sms, stream));
+        in, n_units, ws, reinterpret_cast<unsigned long long *>(len), sms, big_endian, stream));
+}
+
+gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, void *ws,
+                                          size_t ws_bytes, uint64_t *len, cudaStream_t stream)
+{
+    return utf8_length_from_utf16_call(in, n_units, ws, ws_bytes, len, false, stream);
+}
+
+gputf_status gputf_utf16be_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap, void *ws,
+                                   size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, true, stream);
+}
+
+gputf_status gputf_utf8_to_utf16be(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap, void *ws,
+                                   size_t ws_bytes, gputf_result *res, cudaStream_t stream)
+{
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, true, stream);
+}
+
+gputf_status gputf_validate_utf16be(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                    gputf_result *res, cudaStream_t stream)
+{
+    return validate_utf16_call(in, n_units, ws, ws_bytes, res, true, stream);
+}
+
+gputf_status gputf_utf8_length_from_utf16be(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
+                                            uint64_t *len, cudaStream_t stream)
+{
+    return utf8_length_from_utf16_call(in, n_units, ws, ws_bytes, len, true, stream);
 }
 
 gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,

@@ -69,6 +69,13 @@ __device__ __forceinline__ bool load_chunk16(const uint16_t *base, uint64_t e0, 
     return interior;
 }
 
+/* Byte order: UTF-16BE input holds each unit's two bytes the other way
+ * round; swapping them in registers gives the unit values. */
+template <bool BE>
+__device__ __forceinline__ uint32_t units_of(uint32_t w) { return BE ? __byte_perm(w, 0u, 0x2301) : w; }
+template <bool BE>
+__device__ __forceinline__ uint32_t unit_of(uint32_t u) { return BE ? __byte_perm(u, 0u, 0x4401) : u; }
+
 __device__ __forceinline__ bool is_high(uint32_t u) { return (u & 0xFC00) == 0xD800; }
 __device__ __forceinline__ bool is_low(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
 
@@ -186,7 +193,7 @@ struct U16Layout {
  * mbarriers.  Tiles at the ends of the buffer (halo outside the input) are
  * filled by the threads with guarded loads instead.
  */
-template <int THREADS, int UPT, int STAGES, bool VALIDATE>
+template <int THREADS, int UPT, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
@@ -278,12 +285,12 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 #pragma unroll
             for (int v = 0; v < WORDS / 4; v++) {
                 const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
-                w[4 * v + 0] = q.x;
-                w[4 * v + 1] = q.y;
-                w[4 * v + 2] = q.z;
-                w[4 * v + 3] = q.w;
+                w[4 * v + 0] = units_of<BE>(q.x);
+                w[4 * v + 1] = units_of<BE>(q.y);
+                w[4 * v + 2] = units_of<BE>(q.z);
+                w[4 * v + 3] = units_of<BE>(q.w);
             }
-            const uint32_t pu = sb[i0 - 1], nu = sb[i0 + UPT];
+            const uint32_t pu = unit_of<BE>(sb[i0 - 1]), nu = unit_of<BE>(sb[i0 + UPT]);
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
             /* bytes per unit, two units per step (Table 2, with a surrogate
              * pair written whole by its high unit): len8 (1, 2 or 3; 2 for a
@@ -370,12 +377,12 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 #pragma unroll
             for (int v = 0; v < WORDS / 4; v++) {
                 const uint4 q = *reinterpret_cast<const uint4 *>(sb + i0 + 8 * v);
-                w[4 * v + 0] = q.x;
-                w[4 * v + 1] = q.y;
-                w[4 * v + 2] = q.z;
-                w[4 * v + 3] = q.w;
+                w[4 * v + 0] = units_of<BE>(q.x);
+                w[4 * v + 1] = units_of<BE>(q.y);
+                w[4 * v + 2] = units_of<BE>(q.z);
+                w[4 * v + 3] = units_of<BE>(q.w);
             }
-            const uint32_t nu = sb[i0 + UPT];
+            const uint32_t nu = unit_of<BE>(sb[i0 + UPT]);
             /* each unit's bytes, at offsets from the tile's first output byte.
              * Uniform-class fast paths: when every unit of every thread of
              * the warp takes 3 bytes (BMP from U+0800, no surrogate), or 1,
@@ -543,9 +550,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         const uint64_t start = t * TILE > head ? t * TILE - head : 0;
         uint32_t c = 0;
         for (uint64_t i = start + tid; i < pos; i += THREADS) {
-            const uint32_t u = in[i];
-            if (is_high(u)) c += (i + 1 < n && is_low(in[i + 1])) ? 4u : 2u;
-            else if (is_low(u)) c += (i > 0 && is_high(in[i - 1])) ? 0u : 2u;
+            const uint32_t u = unit_of<BE>(in[i]);
+            if (is_high(u)) c += (i + 1 < n && is_low(unit_of<BE>(in[i + 1]))) ? 4u : 2u;
+            else if (is_low(u)) c += (i > 0 && is_high(unit_of<BE>(in[i - 1]))) ? 0u : 2u;
             else c += len8(u);
         }
         uint32_t sum;
@@ -593,7 +600,7 @@ __device__ __forceinline__ uint32_t surrogate_mismatch(const uint32_t (&w)[WORDS
     return bad | ((hcarry != 0) != is_low(nu));
 }
 
-template <int THREADS, int WORDS>
+template <int THREADS, int WORDS, bool BE>
 __global__ void __launch_bounds__(THREADS)
 validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
                       DevResult *res)
@@ -615,10 +622,12 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
         const uint64_t next = tile + gridDim.x;
         uint32_t v[WORDS];
         if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
+#pragma unroll
+        for (int k = 0; k < WORDS; k++) w[k] = units_of<BE>(w[k]);
         uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
         uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
-        if (lane == 0) pu = unit_at(base, (long long)e0 - 1, head, endx);
-        if (lane == 31) nu = unit_at(base, (long long)(e0 + UPT), head, endx);
+        if (lane == 0) pu = unit_of<BE>(unit_at(base, (long long)e0 - 1, head, endx));
+        if (lane == 31) nu = unit_of<BE>(unit_at(base, (long long)(e0 + UPT), head, endx));
         /* units outside the input read as zero, which is no surrogate, so a
          * broken pair always has an input unit to blame */
         if (surrogate_mismatch<WORDS>(w, pu, nu) && first_err == NONE) {
@@ -656,7 +665,7 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
 /* UTF-8 length (Table 2): n + #(u >= 0x80) + #(u >= 0x800) - #surrogates, the
  * three counts taken two units at a time.  A unit outside the input reads as
  * zero and adds nothing. */
-template <int THREADS, int WORDS>
+template <int THREADS, int WORDS, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles,
                               WsHeader *hdr, unsigned long long *len_out)
@@ -680,7 +689,7 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
         uint32_t up = 0, sur = 0;   /* per-half counts in bits 0-15 and 16-31 */
 #pragma unroll
         for (int k = 0; k < WORDS; k++) {
-            const uint32_t x = w[k];
+            const uint32_t x = units_of<BE>(w[k]);
             /* a half >= 0x80: one of bits 7-15 set; >= 0x800: one of bits 11-15 */
             const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
             const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
@@ -713,11 +722,11 @@ uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
     return (((uintptr_t)in % 16) / 2 + n + U16Lay::TILE) / U16Lay::TILE;   /* at least one tile */
 }
 
-template <bool VALIDATE>
+template <bool VALIDATE, bool BE>
 static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap, void *ws,
                             uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE>;
+    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE, BE>;
     static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U16Lay::SMEM);
@@ -737,10 +746,13 @@ static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64
 
 cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 cudaStream_t stream)
+                                 bool big_endian, cudaStream_t stream)
 {
-    return validate ? launch16<true>(in, n, out, cap, ws, status_words, res, sms, stream)
-                    : launch16<false>(in, n, out, cap, ws, status_words, res, sms, stream);
+    if (big_endian)
+        return validate ? launch16<true, true>(in, n, out, cap, ws, status_words, res, sms, stream)
+                        : launch16<false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
+    return validate ? launch16<true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch16<false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no
@@ -758,28 +770,41 @@ static unsigned resident_grid(K kern, int threads, uint64_t tiles, int sms, int 
 }
 
 cudaError_t launch_validate_utf16(const uint16_t *in, uint64_t n, void *ws, DevResult *res,
-                                  int sms, cudaStream_t stream)
+                                  int sms, bool big_endian, cudaStream_t stream)
 {
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 2 * W;
     const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
-    static int per_sm = 0;
-    auto kern = validate_utf16_kernel<T, W>;
-    kern<<<resident_grid(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
-                                                                         res);
+    static int per_sm[2] = {0, 0};
+    if (big_endian) {
+        auto kern = validate_utf16_kernel<T, W, true>;
+        kern<<<resident_grid(kern, T, tiles, sms, &per_sm[1]), T, 0, stream>>>(in, n, tiles,
+                                                                               static_cast<WsHeader *>(ws), res);
+    } else {
+        auto kern = validate_utf16_kernel<T, W, false>;
+        kern<<<resident_grid(kern, T, tiles, sms, &per_sm[0]), T, 0, stream>>>(in, n, tiles,
+                                                                               static_cast<WsHeader *>(ws), res);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_utf8_length_from_utf16(const uint16_t *in, uint64_t n, void *ws,
-                                          unsigned long long *len, int sms, cudaStream_t stream)
+                                          unsigned long long *len, int sms, bool big_endian,
+                                          cudaStream_t stream)
 {
     constexpr int T = 256, W = 8;
     constexpr uint64_t TILE = (uint64_t)T * 2 * W;
     const uint64_t tiles = (((uintptr_t)in % 16) / 2 + n + TILE - 1) / TILE;
-    static int per_sm = 0;
-    auto kern = utf8_length_from_utf16_kernel<T, W>;
-    kern<<<resident_grid(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
-                                                                         len);
+    static int per_sm[2] = {0, 0};
+    if (big_endian) {
+        auto kern = utf8_length_from_utf16_kernel<T, W, true>;
+        kern<<<resident_grid(kern, T, tiles, sms, &per_sm[1]), T, 0, stream>>>(in, n, tiles,
+                                                                               static_cast<WsHeader *>(ws), len);
+    } else {
+        auto kern = utf8_length_from_utf16_kernel<T, W, false>;
+        kern<<<resident_grid(kern, T, tiles, sms, &per_sm[0]), T, 0, stream>>>(in, n, tiles,
+                                                                               static_cast<WsHeader *>(ws), len);
+    }
     return cudaGetLastError();
 }
 

@@ -133,7 +133,7 @@ struct U8Layout {
  * side: the 3 bytes before a position validate it, the 3 after complete a
  * character that starts near the tile's end.
  */
-template <int THREADS, int WORDS, int STAGES, bool VALIDATE>
+template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
@@ -375,10 +375,18 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                         ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
                                         __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
                     }
+                    if (BE) {   /* UTF-16BE: each unit's two bytes the other way round (shift is even) */
+                        ov.x = __byte_perm(ov.x, 0u, 0x2301);
+                        ov.y = __byte_perm(ov.y, 0u, 0x2301);
+                        ov.z = __byte_perm(ov.z, 0u, 0x2301);
+                        ov.w = __byte_perm(ov.w, 0u, 0x2301);
+                    }
                     st_stream16(gbase + lo, ov);
                 } else {
-                    for (uint32_t b = (lo < shift ? shift : lo); b < (hi < lim ? hi : lim); b += 2)
-                        *reinterpret_cast<uint16_t *>(gbase + b) = *reinterpret_cast<const uint16_t *>(outb + b - shift);
+                    for (uint32_t b = (lo < shift ? shift : lo); b < (hi < lim ? hi : lim); b += 2) {
+                        const uint32_t u = *reinterpret_cast<const uint16_t *>(outb + b - shift);
+                        *reinterpret_cast<uint16_t *>(gbase + b) = (uint16_t)(BE ? __byte_perm(u, 0u, 0x4401) : u);
+                    }
                 }
             }
 
@@ -608,11 +616,11 @@ uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
     return ((uintptr_t)in % 16 + n + 1 + U8Lay::TILE - 1) / U8Lay::TILE;
 }
 
-template <bool VALIDATE>
+template <bool VALIDATE, bool BE>
 static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap, void *ws,
                            uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE>;
+    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE, BE>;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U8Lay::SMEM);
@@ -632,10 +640,13 @@ static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_
 
 cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 cudaStream_t stream)
+                                 bool big_endian, cudaStream_t stream)
 {
-    return validate ? launch8<true>(in, n, out, cap, ws, status_words, res, sms, stream)
-                    : launch8<false>(in, n, out, cap, ws, status_words, res, sms, stream);
+    if (big_endian)
+        return validate ? launch8<true, true>(in, n, out, cap, ws, status_words, res, sms, stream)
+                        : launch8<false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
+    return validate ? launch8<true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch8<false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

@@ -359,3 +359,42 @@ def test_output_capacity_stops_at_first_character_that_does_not_fit():
             k = int(np.searchsorted(c8, cap, side="right")) - 1
             assert r == (O.OUTPUT_TOO_SMALL, int(c16[k]), int(c8[k]))
             assert out.tobytes() == u8[:c8[k]].tobytes()
+
+
+# ---------------------------------------------------------------------------
+# UTF-16BE: CPython's utf-16-be codec as the independent routine
+# ---------------------------------------------------------------------------
+def test_utf16be_every_scalar_value_matches_cpython():
+    s = cps_to_str(ALL_SCALARS)
+    u8 = np.frombuffer(s.encode("utf-8"), dtype=np.uint8)
+    be = np.frombuffer(s.encode("utf-16-be"), dtype=">u2").astype(np.uint16)   # units as stored in memory
+    be_mem = np.frombuffer(s.encode("utf-16-be"), dtype=np.uint16)
+    assert not np.array_equal(be, be_mem)
+    r, out16 = O.utf8_to_utf16be(u8)
+    assert r == (O.OK, u8.size, be_mem.size)
+    assert out16.tobytes() == s.encode("utf-16-be")
+    r, out8 = O.utf16be_to_utf8(be_mem)
+    assert r == (O.OK, be_mem.size, u8.size) and out8.tobytes() == u8.tobytes()
+    assert O.validate_utf16be(be_mem) == (O.OK, be_mem.size, 0)
+    assert O.utf8_length_from_utf16be(be_mem) == u8.size
+
+
+def test_utf16be_error_offsets_match_cpython():
+    rng = np.random.default_rng(17)
+    for trial in range(300):
+        t16 = W.utf16_text(3000 + trial, int(rng.integers(1, 200)), W.SCRIPT_MIXED)
+        bad = t16.copy()
+        for _ in range(int(rng.integers(0, 3))):
+            bad[int(rng.integers(0, bad.size))] = int(rng.integers(0xD700, 0xE100))
+        mem = np.frombuffer(bad.astype(">u2").tobytes(), dtype=np.uint16)   # big-endian storage
+        try:
+            mem.tobytes().decode("utf-16-be")
+            start = None
+        except UnicodeDecodeError as e:
+            start = e.start // 2
+        r = O.validate_utf16be(mem)
+        assert r.position == (bad.size if start is None else start)
+        assert (r.error == O.OK) == (start is None)
+        r2, out = O.utf16be_to_utf8(mem)
+        assert (r2.error, r2.position) == (r.error, r.position)
+        assert out.tobytes() == mem[:r.position].tobytes().decode("utf-16-be").encode("utf-8")

@@ -94,16 +94,14 @@ __device__ __forceinline__ uint32_t zero_halves(uint32_t x)
     return (x - 0x00010001u) & ~x & 0x80008000u;
 }
 
-/* Sum of the eight 4-bit fields of x (each at most 8). */
-__device__ __forceinline__ uint32_t nibble_sum(uint32_t x)
-{
-    return (((x & 0x0F0F0F0Fu) + ((x >> 4) & 0x0F0F0F0Fu)) * 0x01010101u) >> 24;
-}
+/* Sum of the four bytes of x (the sum below 256). */
+__device__ __forceinline__ uint32_t byte_sum(uint32_t x) { return (x * 0x01010101u) >> 24; }
 
-/* Append `len` bytes held in `v` to a thread's run of staged bytes.  Full
- * words are stored; the first word (when the run starts inside a word) and
- * the last partial word are shared with the neighbouring threads' runs and
- * are OR-ed into the zeroed staging buffer. */
+/* Byte j of x, zero-extended (one instruction for a constant j). */
+__device__ __forceinline__ uint32_t byte_at(uint32_t x, int j)
+{
+    return j == 0 ? (x & 0xFFu) : j == 3 ? (x >> 24) : __byte_perm(x, 0u, 0x4440u + (uint32_t)j);
+}
 
 /* Output bytes of a unit by value: 1, 2 or 3, and 2 for a surrogate unit
  * (the closed form of the length pass; Table 2). */
@@ -112,14 +110,10 @@ __device__ __forceinline__ uint32_t len8(uint32_t u)
     return u < 0x80 ? 1u : ((u < 0x800 || (u & 0xF800) == 0xD800) ? 2u : 3u);
 }
 
-/* Spreads the 8 low bits of x to bit 0 of the eight 4-bit fields of a word. */
-__device__ __forceinline__ uint32_t spread4(uint32_t x)
+/* 0xFF in byte i of the result for each set bit i of the 4 low bits of x. */
+__device__ __forceinline__ uint32_t byte_mask4(uint32_t x)
 {
-    x &= 0xFF;
-    x = (x | (x << 12)) & 0x000F000Fu;
-    x = (x | (x << 6)) & 0x03030303u;
-    x = (x | (x << 3)) & 0x11111111u;
-    return x;
+    return (((x & 0xFu) * 0x00204081u) & 0x01010101u) * 0xFFu;
 }
 
 /*
@@ -137,12 +131,11 @@ __device__ __forceinline__ uint32_t spread4(uint32_t x)
  * 110 / 1110 / 11110 and continuation prefix 10.)  A lone surrogate (an
  * error) writes 2 bytes of no meaning; they lie past the valid prefix.
  */
-__device__ __forceinline__ void put_utf8(uint8_t *dst, uint32_t o, uint32_t u, uint32_t next, uint32_t l)
+__device__ __forceinline__ void put_utf8(uint32_t sa, uint32_t u, uint32_t next, uint32_t l)
 {
     const uint32_t c = (u << 10) + next - 0x35FDC00u;
     const uint32_t y = l == 4 ? c : u;
-    const uint32_t sa = smem_u32(dst) + o;           /* shared-space address of the lead byte */
-    const uint32_t se = sa + l;                        /* one past the last byte */
+    const uint32_t se = sa + l;                        /* sa: shared address of the lead byte; se: one past the last */
     const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __funnelshift_r(0xF0E0C000u, 0u, 8 * l - 8);
     const uint32_t b1 = (y & 0x3F) | 0x80, b2 = ((y >> 6) & 0x3F) | 0x80, b3 = ((y >> 12) & 0x3F) | 0x80;
     /* predicated stores: lead at o, continuation bytes at end-1, end-2, end-3
@@ -157,6 +150,34 @@ __device__ __forceinline__ void put_utf8(uint8_t *dst, uint32_t o, uint32_t u, u
                  "@p3 st.shared.u8 [%5+-2], %3;\n\t"
                  "@p4 st.shared.u8 [%5+-3], %6;\n\t}"
                  :: "r"(sa), "r"(lead), "r"(b1), "r"(b2), "r"(l), "r"(se), "r"(b3) : "memory");
+}
+
+/*
+ * The same bytes, written back to front: the unit's bytes end at shared
+ * address e (exclusive); returns its start e - l.  The continuation-byte
+ * positions e-3, e-2, e-1 are stored unconditionally and the lead byte last,
+ * so a unit shorter than 4 bytes leaves stray bytes below its start, in the
+ * bytes of the units before it.  Units therefore go in reverse order (each
+ * unit's earlier neighbours overwrite its strays), and the caller keeps e - 3
+ * at or above the start of the thread's run.  Only the lead store needs a
+ * predicate (a unit of 0 bytes writes nothing of its own).
+ */
+__device__ __forceinline__ uint32_t put_utf8_back(uint32_t e, uint32_t u, uint32_t next, uint32_t l)
+{
+    const uint32_t c = (u << 10) + next - 0x35FDC00u;
+    const uint32_t y = l == 4 ? c : u;
+    const uint32_t s = e - l;
+    /* lead prefix by length: bytes 0x00, 0xC0, 0xE0 of the first word, 0xF0 of the second */
+    const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __byte_perm(0xE0C00000u, 0xF0u, l);
+    const uint32_t b1 = (y & 0x3F) | 0x80, b2 = ((y >> 6) & 0x3F) | 0x80, b3 = ((c >> 12) & 0x3F) | 0x80;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.u32 p, %4, 0;\n\t"
+                 "st.shared.u8 [%0+-3], %3;\n\t"
+                 "st.shared.u8 [%0+-2], %2;\n\t"
+                 "st.shared.u8 [%0+-1], %1;\n\t"
+                 "@p st.shared.u8 [%5], %6;\n\t}"
+                 :: "r"(e), "r"(b1), "r"(b2), "r"(b3), "r"(l), "r"(s), "r"(lead) : "memory");
+    return s;
 }
 
 constexpr int HALO16 = 8;   /* units staged on each side of a tile (16 bytes) */
@@ -203,7 +224,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
     constexpr int WORDS = UPT / 2;
-    constexpr int NW = UPT / 8;   /* words of 4-bit per-unit byte counts */
+    constexpr int NL = UPT / 4;   /* words of per-unit byte counts, one byte a unit */
     static_assert(UPT % 8 == 0 && UPT <= 32, "units per thread: a multiple of 8, at most 32");
     static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
     extern __shared__ uint4 smem4[];
@@ -250,10 +271,11 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     /* state of tile c (phase A done, phase B pending) */
     bool have_c = false;
     unsigned long long c_tile = 0;
-    uint32_t c_total = 0, c_excl = 0, c_nib[NW];
+    uint32_t c_total = 0, c_end = 0, c_len[NL];   /* c_end: end of the thread's bytes, from the tile's first byte */
 #pragma unroll
-    for (int j = 0; j < NW; j++) c_nib[j] = 0;
+    for (int j = 0; j < NL; j++) c_len[j] = 0;
     int c_stage = 0;
+    bool c_whole = false;   /* every unit of tile c lies inside the input */
 
 #define UNIT(k) ((w[(k) / 2] >> (16 * ((k) & 1))) & 0xFFFFu)
     for (int it = 0;; it++) {
@@ -266,9 +288,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         const int sn = it % STAGES;
         const unsigned long long t = s_ring[sn];
         const bool have_n = t < tiles;
-        uint32_t n_total = 0, n_excl = 0, n_nib[NW];
+        uint32_t n_total = 0, n_end = 0, n_len[NL];
 #pragma unroll
-        for (int j = 0; j < NW; j++) n_nib[j] = 0;
+        for (int j = 0; j < NL; j++) n_len[j] = 0;
         if (have_n) {
             const uint64_t x0 = t * TILE;
             uint16_t *sb = stages + (size_t)sn * Lay::STAGE_UNITS;
@@ -292,47 +314,66 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             }
             const uint32_t pu = unit_of<BE>(sb[i0 - 1]), nu = unit_of<BE>(sb[i0 + UPT]);
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
-            /* bytes per unit, two units per step (Table 2, with a surrogate
-             * pair written whole by its high unit): len8 (1, 2 or 3; 2 for a
-             * surrogate), plus 2 for a high unit followed by a low one, minus
-             * 2 for a low unit that follows a high one, so a pair gives 4 + 0
-             * and a lone surrogate 2: no tile needs more than 3 bytes a unit
-             * (plus one for a pair cut by the tile's end).  A word's "next
-             * unit is low" flags need the next word, so each word is
-             * finished one step later.  Section 3's pairing rule is checked
-             * as "the unit before is high" == "this unit is low" for every
-             * two adjacent units. */
-            uint32_t lanes = 0, bad = 0, hcarry = is_high(pu) ? 0x8000u : 0u;
-            uint32_t p_base = 0, p_hi = 0, p_lo = 0, p_ph = 0;   /* the word before */
+            /* bytes per unit (Table 2, with a surrogate pair written whole
+             * by its high unit): 1 below 0x80, 2 below 0x800, 3 for the rest
+             * of the BMP, 4 for a high unit followed by a low one, 0 for that
+             * low unit, and 2 for a lone surrogate, so no tile needs more than
+             * 3 bytes a unit (plus one for a pair cut by the tile's end).
+             * Two units per step, as flags at bits 15 and 31 of a word:
+             *   N: not the low half of a pair (counts 1),
+             *   A: counts one more (2-byte units and surrogates other than a
+             *      pair's low half),
+             *   B: counts two more (3-byte units and a pair's high half);
+             * a word's B needs the "next unit is low" flags of the word after
+             * it, so each word is finished one step later, and each two
+             * finished words are gathered into one byte per unit.  Section
+             * 3's pairing rule is checked as "the unit before is high" ==
+             * "this unit is low" for every two adjacent units. */
+            uint32_t lens = 0, bad = 0;
+            uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* bit 31: the unit before the word is high */
+            uint32_t p_c2 = 0, p_hi = 0, p_lo = 0, p_N = 0, p_A = 0;   /* the word before */
+            uint32_t q_N = 0, q_A = 0, q_B = 0;                     /* the even word of a finished pair */
 #pragma unroll
             for (int k = 0; k <= WORDS; k++) {
-                uint32_t base = 0, hi = 0, lo = is_low(nu) ? 0x8000u : 0u, ph = 0;
+                uint32_t hi = 0, lo = is_low(nu) ? 0x8000u : 0u, c2 = 0, N = 0, A = 0;
                 if (k < WORDS) {
                     const uint32_t x = w[k];
                     const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
                     const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-                    const uint32_t sg = (x & 0xFC00FC00u) ^ 0xD800D800u;
-                    hi = zero_halves(sg);
-                    lo = zero_halves(sg ^ 0x04000400u);
-                    /* len8 per half (0..3) in bits 0-1 and 16-17 */
-                    base = 0x00010001u + (ge80 >> 15) + (ge800 >> 15) - ((hi | lo) >> 15);
-                    ph = (hi << 16) | hcarry;   /* bit 15: unit 2k-1 is high; bit 31: unit 2k is high */
+                    const uint32_t sur = zero_halves((x & 0xF800F800u) ^ 0xD800D800u);
+                    const uint32_t t = x << 5;   /* bit 10 of each unit (low surrogate) to bit 15 / 31 */
+                    hi = sur & ~t;
+                    lo = sur & t;
+                    const uint32_t ph = __byte_perm(hprev, hi, 0x5432);   /* the unit before each unit is high */
                     if (VALIDATE) bad |= ph ^ lo;
-                    hcarry = hi >> 16;
+                    hprev = hi;
+                    c2 = ge800 & ~sur;                  /* 3-byte unit */
+                    N = ~(lo & ph) & 0x80008000u;
+                    A = (ge80 ^ c2) & N;
                 }
                 if (k > 0) {   /* finish word k-1 */
                     const uint32_t nl = __funnelshift_r(p_lo, lo, 16);   /* its units' next unit is low */
-                    const uint32_t L = p_base + ((p_hi & nl) >> 14) - ((p_lo & p_ph) >> 14);
-                    lanes += L;
-                    n_nib[(k - 1) / 4] |= ((L | (L >> 12)) & 0xFFu) << (8 * ((k - 1) % 4));
+                    const uint32_t B = p_c2 | (p_hi & nl);
+                    if ((k - 1) % 2 == 0) {
+                        q_N = p_N;
+                        q_A = p_A;
+                        q_B = B;
+                    } else {   /* bytes of units 4j .. 4j+3 from the flags at bits 15 / 31 of words 2j, 2j+1 */
+                        const uint32_t L = (__byte_perm(q_N, p_N, 0x7531) >> 7) +
+                                           (__byte_perm(q_A, p_A, 0x7531) >> 7) +
+                                           (__byte_perm(q_B, B, 0x7531) >> 6);
+                        n_len[(k - 1) / 2] = L;
+                        lens += L;
+                    }
                 }
-                p_base = base;
+                p_c2 = c2;
                 p_hi = hi;
                 p_lo = lo;
-                p_ph = ph;
+                p_N = N;
+                p_A = A;
             }
-            if (VALIDATE) bad |= (uint32_t)((hcarry != 0) != is_low(nu));
-            n_total = (lanes & 0xFFFF) + (lanes >> 16);
+            if (VALIDATE) bad |= (uint32_t)((hprev >> 31) != (is_low(nu) ? 1u : 0u));
+            n_total = byte_sum(lens);
             uint32_t inr = 0xFFFFFFFFu;
             if (!interior) {   /* units outside the input write nothing */
                 inr = 0;
@@ -341,9 +382,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                     inr |= (e0 + k >= (long long)head && e0 + k < (long long)endx) ? (1u << k) : 0u;
                 n_total = 0;
 #pragma unroll
-                for (int j = 0; j < NW; j++) {
-                    n_nib[j] &= spread4(inr >> (8 * j)) * 0xFu;
-                    n_total += nibble_sum(n_nib[j]);
+                for (int j = 0; j < NL; j++) {
+                    n_len[j] &= byte_mask4(inr >> (4 * j));
+                    n_total += byte_sum(n_len[j]);
                 }
             }
             uint64_t first_err = NONE;
@@ -359,7 +400,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 }
             }
             bool any_err;
-            n_excl = block_exclusive_or<THREADS>(n_total, first_err != NONE, s_warp, &n_total, &any_err);
+            n_end = n_total + block_exclusive_or<THREADS>(n_total, first_err != NONE, s_warp, &n_total, &any_err);
             if (tid == 0)
                 st_release(status + t, make_status(epoch, t == 0 ? ST_PREFIX : ST_AGGREGATE, n_total));
             if (any_err) {
@@ -388,14 +429,14 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
              * the warp takes 3 bytes (BMP from U+0800, no surrogate), or 1,
              * or 2, the bytes go to fixed offsets with no per-unit length
              * work (the same bytes the general path writes). */
-            uint32_t nib_and = c_nib[0], nib_or = c_nib[0];
+            uint32_t len_and = c_len[0], len_or = c_len[0];
 #pragma unroll
-            for (int j = 1; j < NW; j++) {
-                nib_and &= c_nib[j];
-                nib_or |= c_nib[j];
+            for (int j = 1; j < NL; j++) {
+                len_and &= c_len[j];
+                len_or |= c_len[j];
             }
-            uint8_t *dst = outb + c_excl;
-            if (__all_sync(FULL_MASK, nib_and == 0x33333333u && nib_or == 0x33333333u)) {
+            if (__all_sync(FULL_MASK, len_and == 0x03030303u && len_or == 0x03030303u)) {
+                uint8_t *dst = outb + c_end - 3 * UPT;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
                     const uint32_t u = UNIT(k);
@@ -403,23 +444,43 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                     dst[3 * k + 1] = (uint8_t)(0x80 | ((u >> 6) & 0x3F));
                     dst[3 * k + 2] = (uint8_t)(0x80 | (u & 0x3F));
                 }
-            } else if (__all_sync(FULL_MASK, nib_and == 0x11111111u && nib_or == 0x11111111u)) {
+            } else if (__all_sync(FULL_MASK, len_and == 0x01010101u && len_or == 0x01010101u)) {
+                uint8_t *dst = outb + c_end - UPT;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) dst[k] = (uint8_t)UNIT(k);
-            } else if (__all_sync(FULL_MASK, nib_and == 0x22222222u && nib_or == 0x22222222u)) {
+            } else if (__all_sync(FULL_MASK, len_and == 0x02020202u && len_or == 0x02020202u)) {
+                uint8_t *dst = outb + c_end - 2 * UPT;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
                     const uint32_t u = UNIT(k);
                     dst[2 * k] = (uint8_t)(0xC0 | (u >> 6));
                     dst[2 * k + 1] = (uint8_t)(0x80 | (u & 0x3F));
                 }
-            } else {
-                uint32_t o = c_excl;
+            } else if (c_whole) {
+                /* every unit of the tile is inside the input: units 3.. go
+                 * back to front with unconditional stores, then units 2, 1, 0
+                 * exactly.  The strays stay inside the thread's run because
+                 * units 0-3 take at least 3 bytes: only the low half of a
+                 * pair takes none, and if that is unit 1, 2 or 3, its high
+                 * half is unit 0, 1 or 2 and takes 4. */
+                uint32_t e = smem_u32(outb) + c_end;
 #pragma unroll
-                for (int k = 0; k < UPT; k++) {
-                    const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
-                    put_utf8(outb, o, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
-                    o += l;
+                for (int k = UPT - 1; k >= 3; k--)
+                    e = put_utf8_back(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu,
+                                      byte_at(c_len[k / 4], k % 4));
+#pragma unroll
+                for (int k = 2; k >= 0; k--) {
+                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
+                    e -= l;
+                    put_utf8(e, UNIT(k), UNIT(k + 1), l);
+                }
+            } else {
+                uint32_t e = smem_u32(outb) + c_end;
+#pragma unroll
+                for (int k = UPT - 1; k >= 0; k--) {
+                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
+                    e -= l;
+                    put_utf8(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
                 }
             }
 
@@ -493,10 +554,13 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             if (G0 <= cap && G0 + c_total > cap) {
                 const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * UPT);
                 uint64_t cap_first = NONE;
-                uint64_t g = G0 + c_excl;
+                uint32_t own = 0;
+#pragma unroll
+                for (int j = 0; j < NL; j++) own += byte_sum(c_len[j]);
+                uint64_t g = G0 + c_end - own;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {
-                    const uint32_t l = (c_nib[k / 8] >> (4 * (k % 8))) & 0xF;
+                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
                     if (l && g + l > cap && cap_first == NONE) cap_first = (uint64_t)(e0 + k) - head;
                     g += l;
                 }
@@ -512,9 +576,10 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         have_c = true;
         c_tile = t;
         c_total = n_total;
-        c_excl = n_excl;
+        c_end = n_end;
+        c_whole = t * TILE >= head && t * TILE + TILE <= endx;
 #pragma unroll
-        for (int j = 0; j < NW; j++) c_nib[j] = n_nib[j];
+        for (int j = 0; j < NL; j++) c_len[j] = n_len[j];
         c_stage = sn;
         __syncthreads();
     }

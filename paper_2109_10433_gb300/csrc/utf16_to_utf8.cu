@@ -238,6 +238,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     __shared__ unsigned long long s_min[WARPS];
     __shared__ unsigned long long s_lb_sum[WARPS];
     __shared__ unsigned s_lb_has[WARPS];
+    __shared__ unsigned long long s_lb_g0;
     __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x;
@@ -503,17 +504,24 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                     s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
                 }
                 __syncthreads();
-                bool found = false, usable = true;
+                /* warp 0 combines the warps' partials: the sums of the warps
+                 * up to the first one that saw a prefix, usable when no warp
+                 * up to that one saw an unpublished entry */
+                if (wid == 0) {
+                    const unsigned h = lane < WARPS ? s_lb_has[lane] : 1u;
+                    const uint64_t sum = lane < WARPS ? s_lb_sum[lane] : 0;
+                    const unsigned pm = __ballot_sync(FULL_MASK, (h & 1u) != 0);   /* lanes >= WARPS: a prefix */
+                    const int first = __ffs(pm) - 1;
+                    const bool usable = (__ballot_sync(FULL_MASK, (h & 2u) != 0) & ((2u << first) - 1)) == 0 &&
+                                        first < WARPS;
+                    uint64_t v = lane <= first ? sum : 0;
 #pragma unroll
-                for (int k = 0; k < WARPS; k++) {
-                    if (!found && usable) {
-                        usable = (s_lb_has[k] & 2u) == 0;
-                        G0 += s_lb_sum[k];
-                        found = (s_lb_has[k] & 1u) != 0;
-                    }
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+                    if (lane == 0) s_lb_g0 = usable ? v : ~0ull;
                 }
                 __syncthreads();
-                if (!(found && usable))   /* rare: poll until the predecessors publish */
+                G0 = s_lb_g0;
+                if (G0 == ~0ull)   /* poll until the predecessors publish */
                     G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
                 if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
             } else {
@@ -570,7 +578,9 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             __syncthreads();
         }
 
-        /* tile n becomes c; a new tile goes in flight into c's old stage */
+        /* tile n becomes c; a new tile goes in flight into c's old stage,
+         * whose reads phase B's last barrier has retired (and which no
+         * thread reads again before the next iteration's barriers) */
         if (!have_n) break;
         if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
         have_c = true;
@@ -581,7 +591,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 #pragma unroll
         for (int j = 0; j < NL; j++) c_len[j] = n_len[j];
         c_stage = sn;
-        __syncthreads();
     }
 #undef UNIT
 

@@ -198,18 +198,21 @@ struct U16Layout {
  * before it:
  *   phase A(n): bytes per unit, validation, block scan; publish n's aggregate
  *               (and its first error);
- *   phase B(c): c's exclusive output offset by decoupled look-back (its
+ *   phase B(c): c's bytes into the staging buffer at tile-local offsets;
+ *               c's exclusive output offset by decoupled look-back (its
  *               status words are requested at the top of the iteration and
- *               examined after the bytes are written); c's bytes into the staging buffer at
- *               tile-local offsets; publish c's inclusive prefix; write the
- *               tile out with aligned 16-byte stores;
- *   then take a new ticket and start its input copy into the freed stage.
- * Every look-back thus runs one iteration after its tile's aggregate went
- * out, when the tiles before it have long published theirs, and a CTA only
- * waits (in a look-back) while every ticket it holds has its aggregate
- * published: no tile ever waits behind work queued in another CTA.
+ *               examined after the bytes are written); the next tile's
+ *               input copy starts into c's stage, now read; publish c's
+ *               inclusive prefix; write the tile out with aligned 16-byte
+ *               stores.
+ * The ticket for that next tile is taken when its copy starts, so a tile's
+ * aggregate goes out about half an iteration after its ticket, and its
+ * look-back runs about one iteration after that.  A look-back waits only
+ * for the aggregates of smaller tickets, and a CTA's pending look-back is
+ * always for a ticket smaller than any it holds unpublished, so the CTA
+ * holding the smallest unpublished ticket never waits: every wait ends.
  *
- * Input tiles (plus 8 units of halo on each side) arrive in a three-stage
+ * Input tiles (plus 8 units of halo on each side) arrive in a two-stage
  * shared-memory ring by 1-D TMA bulk copies completing on per-stage
  * mbarriers.  Tiles at the ends of the buffer (halo outside the input) are
  * filled by the threads with guarded loads instead.
@@ -226,7 +229,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     constexpr int WORDS = UPT / 2;
     constexpr int NL = UPT / 4;   /* words of per-unit byte counts, one byte a unit */
     static_assert(UPT % 8 == 0 && UPT <= 32, "units per thread: a multiple of 8, at most 32");
-    static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
+    static_assert(STAGES == 2, "tile in phase A, tile in phase B (whose stage is refilled mid-iteration)");
     extern __shared__ uint4 smem4[];
     uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
     uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
@@ -527,6 +530,10 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             } else {
                 __syncthreads();
             }
+            /* every thread has read c's stage: a new ticket's tile goes in
+             * flight into it (a ticket taken this late keeps the tiles in
+             * flight close together, so look-backs seldom wait) */
+            if (tid == 0 && have_n) issue(atomicAdd(&hdr->ticket, 1ull), c_stage);
 
             /* write the tile's output bytes [G0, G0 + cnt), clipped to the
              * capacity: aligned 16-byte stores, each assembled from the
@@ -578,11 +585,8 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             __syncthreads();
         }
 
-        /* tile n becomes c; a new tile goes in flight into c's old stage,
-         * whose reads phase B's last barrier has retired (and which no
-         * thread reads again before the next iteration's barriers) */
+        /* tile n becomes c */
         if (!have_n) break;
-        if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
         have_c = true;
         c_tile = t;
         c_total = n_total;
@@ -788,7 +792,7 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
  * ---------------------------------------------------------------------- */
 constexpr int U16_THREADS = 256;
 constexpr int U16_UPT = 24;     /* 6144-unit tiles */
-constexpr int U16_STAGES = 3;
+constexpr int U16_STAGES = 2;
 using U16Lay = U16Layout<U16_THREADS, U16_UPT, U16_STAGES>;
 
 uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)

@@ -127,11 +127,12 @@ struct U8Layout {
  * Persistent transcoder, software-pipelined over tiles (the same schedule as
  * the UTF-16 -> UTF-8 kernel): each iteration runs phase A of the tile n
  * whose input just arrived (lengths, validation, block scan, aggregate) and
- * phase B of the tile c before it (look-back, decode into the staging buffer,
- * inclusive prefix, write-out), then takes a new ticket and starts its input
- * copy into the stage c used.  Input arrives with 16 bytes of halo on each
- * side: the 3 bytes before a position validate it, the 3 after complete a
- * character that starts near the tile's end.
+ * phase B of the tile c before it (decode into the staging buffer,
+ * look-back, inclusive prefix, write-out); as soon as the decoding has read
+ * c's stage, a new ticket is taken and its input copy starts into that stage
+ * (a two-stage ring).  Input arrives with 16 bytes of halo on each side: the
+ * 3 bytes before a position validate it, the 3 after complete a character
+ * that starts near the tile's end.
  */
 template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
@@ -143,7 +144,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     constexpr int BPT = Lay::BPT;
     constexpr uint64_t TILE = Lay::TILE;
     constexpr int WARPS = THREADS / 32;
-    static_assert(STAGES == 3, "tile in phase A, tile in phase B, tile in flight");
+    static_assert(STAGES == 2, "tile in phase A, tile in phase B (whose stage is refilled mid-iteration)");
     extern __shared__ uint4 smem4[];
     uint8_t *stages = reinterpret_cast<uint8_t *>(smem4);
     uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
@@ -156,6 +157,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     __shared__ unsigned long long s_min[WARPS];
     __shared__ unsigned long long s_lb_sum[WARPS];
     __shared__ unsigned s_lb_has[WARPS];
+    __shared__ unsigned long long s_lb_g0;
     __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x;
@@ -338,22 +340,33 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
                 }
                 __syncthreads();
-                bool found = false, usable = true;
+                /* warp 0 combines the warps' partials: the sums of the warps
+                 * up to the first one that saw a prefix, usable when no warp
+                 * up to that one saw an unpublished entry */
+                if (wid == 0) {
+                    const unsigned h = lane < WARPS ? s_lb_has[lane] : 1u;
+                    const uint64_t sum = lane < WARPS ? s_lb_sum[lane] : 0;
+                    const unsigned pm = __ballot_sync(FULL_MASK, (h & 1u) != 0);   /* lanes >= WARPS: a prefix */
+                    const int first = __ffs(pm) - 1;
+                    const bool usable = (__ballot_sync(FULL_MASK, (h & 2u) != 0) & ((2u << first) - 1)) == 0 &&
+                                        first < WARPS;
+                    uint64_t v = lane <= first ? sum : 0;
 #pragma unroll
-                for (int k = 0; k < WARPS; k++) {
-                    if (!found && usable) {
-                        usable = (s_lb_has[k] & 2u) == 0;
-                        G0 += s_lb_sum[k];
-                        found = (s_lb_has[k] & 1u) != 0;
-                    }
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+                    if (lane == 0) s_lb_g0 = usable ? v : ~0ull;
                 }
                 __syncthreads();
-                if (!(found && usable))
+                G0 = s_lb_g0;
+                if (G0 == ~0ull)   /* poll until the predecessors publish */
                     G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
                 if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
             } else {
                 __syncthreads();
             }
+            /* every thread has read c's stage: a new ticket's tile goes in
+             * flight into it (a ticket taken this late keeps the tiles in
+             * flight close together, so look-backs seldom wait) */
+            if (tid == 0 && have_n) issue(atomicAdd(&hdr->ticket, 1ull), c_stage);
 
             /* write the tile's units [G0, G0 + cnt), clipped to the capacity,
              * with aligned 16-byte stores assembled by funnel shifts */
@@ -413,14 +426,12 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
         }
 
         if (!have_n) break;
-        if (tid == 0) issue(atomicAdd(&hdr->ticket, 1ull), (it + 2) % STAGES);
         have_c = true;
         c_interior = interior;
         c_tile = t;
         c_total = n_total;
         c_excl = n_excl;
         c_stage = sn;
-        __syncthreads();
     }
 
     /* the CTA that finishes last writes the result */
@@ -606,7 +617,7 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
  * ---------------------------------------------------------------------- */
 constexpr int U8_THREADS = 256;
 constexpr int U8_WORDS = 8;     /* 32 bytes per thread, 8 KiB tiles */
-constexpr int U8_STAGES = 3;
+constexpr int U8_STAGES = 2;
 using U8Lay = U8Layout<U8_THREADS, U8_WORDS, U8_STAGES>;
 
 uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)

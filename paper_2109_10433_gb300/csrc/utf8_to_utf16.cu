@@ -155,12 +155,10 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     __shared__ unsigned long long s_ring[STAGES];
     __shared__ uint32_t s_warp[WARPS + 2];
     __shared__ unsigned long long s_min[WARPS];
-    __shared__ unsigned long long s_lb_sum[WARPS];
-    __shared__ unsigned s_lb_has[WARPS];
     __shared__ unsigned long long s_lb_g0;
     __shared__ unsigned s_flag;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint64_t head = (uintptr_t)in & 15;
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;    /* extended index of the end position */
@@ -272,8 +270,8 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             const uint8_t *sb = stages + (size_t)c_stage * Lay::STAGE_BYTES;
             const int i0 = HALO8 + tid * BPT;
             const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * BPT);
-            const long long lb_idx = (long long)c_tile - 1 - tid;
-            const uint64_t lb_word = (c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
+            const long long lb_idx = (long long)c_tile - 1 - tid;   /* warp 0's lanes */
+            const uint64_t lb_word = (tid < 32 && c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
 
             uint32_t w[WORDS];
 #pragma unroll
@@ -323,46 +321,31 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                 }
             }
 
-            uint64_t G0 = 0;
-            if (c_tile > 0) {
+            /* c's exclusive output offset, by warp 0 alone: its window (the
+             * 32 tiles before c) is usable when an inclusive prefix appears in
+             * it and every entry before that one has been published; otherwise
+             * the warp walks back, waiting (bounded) for each word.  The
+             * barrier then marks the staging buffer complete and hands G0 to
+             * every thread. */
+            if (c_tile > 0 && wid == 0) {
                 const bool in_window = lb_idx >= 0;
                 const uint64_t flag = in_window ? ((lb_word >> 40) & 3) : ST_PREFIX;
                 const bool ok = !in_window || ((unsigned)(lb_word >> 43) == epoch && flag != 0);
                 const unsigned pmask = __ballot_sync(FULL_MASK, ok && flag == ST_PREFIX);
-                const unsigned bad = __ballot_sync(FULL_MASK, !ok);
-                const int lane = tid & 31, wid = tid >> 5;
+                const unsigned badm = __ballot_sync(FULL_MASK, !ok);
                 const int stop = pmask ? __ffs(pmask) - 1 : 31;
                 uint64_t v = (lane <= stop && in_window) ? (lb_word & VALUE_MASK) : 0;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+                if (!pmask || (badm & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))))
+                    v = look_back(status, (long long)c_tile, epoch, &hdr->flags);
                 if (lane == 0) {
-                    s_lb_sum[wid] = v;
-                    s_lb_has[wid] = (pmask ? 1u : 0u) | ((bad & (stop == 31 ? FULL_MASK : ((2u << stop) - 1))) ? 2u : 0u);
+                    s_lb_g0 = v;
+                    st_release(status + c_tile, make_status(epoch, ST_PREFIX, v + c_total));
                 }
-                __syncthreads();
-                /* warp 0 combines the warps' partials: the sums of the warps
-                 * up to the first one that saw a prefix, usable when no warp
-                 * up to that one saw an unpublished entry */
-                if (wid == 0) {
-                    const unsigned h = lane < WARPS ? s_lb_has[lane] : 1u;
-                    const uint64_t sum = lane < WARPS ? s_lb_sum[lane] : 0;
-                    const unsigned pm = __ballot_sync(FULL_MASK, (h & 1u) != 0);   /* lanes >= WARPS: a prefix */
-                    const int first = __ffs(pm) - 1;
-                    const bool usable = (__ballot_sync(FULL_MASK, (h & 2u) != 0) & ((2u << first) - 1)) == 0 &&
-                                        first < WARPS;
-                    uint64_t v = lane <= first ? sum : 0;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
-                    if (lane == 0) s_lb_g0 = usable ? v : ~0ull;
-                }
-                __syncthreads();
-                G0 = s_lb_g0;
-                if (G0 == ~0ull)   /* poll until the predecessors publish */
-                    G0 = block_look_back<THREADS>(status, (long long)c_tile, epoch, &hdr->flags, s_lb_sum, s_lb_has);
-                if (tid == 0) st_release(status + c_tile, make_status(epoch, ST_PREFIX, G0 + c_total));
-            } else {
-                __syncthreads();
             }
+            __syncthreads();
+            const uint64_t G0 = c_tile > 0 ? s_lb_g0 : 0;
             /* every thread has read c's stage: a new ticket's tile goes in
              * flight into it (a ticket taken this late keeps the tiles in
              * flight close together, so look-backs seldom wait) */

@@ -94,6 +94,13 @@ __device__ __forceinline__ uint32_t zero_halves(uint32_t x)
     return (x - 0x00010001u) & ~x & 0x80008000u;
 }
 
+/* Bit 7 of each byte: set when that byte of x is zero (exact per byte: no
+ * carry crosses a byte). */
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x)
+{
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
 /* Sum of the four bytes of x (the sum below 256). */
 __device__ __forceinline__ uint32_t byte_sum(uint32_t x) { return (x * 0x01010101u) >> 24; }
 
@@ -321,54 +328,47 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
              * of the BMP, 4 for a high unit followed by a low one, 0 for that
              * low unit, and 2 for a lone surrogate, so no tile needs more than
              * 3 bytes a unit (plus one for a pair cut by the tile's end).
-             * Two units per step, as flags at bits 15 and 31 of a word:
+             * Four units per step: their high bytes (and low bytes) gathered
+             * into one word by a byte permute, classified with exact per-byte
+             * tests, as flags at bit 7 of each byte:
              *   N: not the low half of a pair (counts 1),
              *   A: counts one more (2-byte units and surrogates other than a
              *      pair's low half),
              *   B: counts two more (3-byte units and a pair's high half);
-             * a word's B needs the "next unit is low" flags of the word after
-             * it, so each word is finished one step later, and each two
-             * finished words are gathered into one byte per unit.  Section
+             * a group's B needs the "next unit is low" flags of the group
+             * after it, so each group is finished one step later.  Section
              * 3's pairing rule is checked as "the unit before is high" ==
              * "this unit is low" for every two adjacent units. */
             uint32_t lens = 0, bad = 0;
-            uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* bit 31: the unit before the word is high */
-            uint32_t p_c2 = 0, p_hi = 0, p_lo = 0, p_N = 0, p_A = 0;   /* the word before */
-            uint32_t q_N = 0, q_A = 0, q_B = 0;                     /* the even word of a finished pair */
+            uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* byte 3: the unit before the group is high */
+            uint32_t p_c3 = 0, p_hi = 0, p_lo = 0, p_N = 0, p_A = 0;   /* the group before */
 #pragma unroll
-            for (int k = 0; k <= WORDS; k++) {
-                uint32_t hi = 0, lo = is_low(nu) ? 0x8000u : 0u, c2 = 0, N = 0, A = 0;
-                if (k < WORDS) {
-                    const uint32_t x = w[k];
-                    const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-                    const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-                    const uint32_t sur = zero_halves((x & 0xF800F800u) ^ 0xD800D800u);
-                    const uint32_t t = x << 5;   /* bit 10 of each unit (low surrogate) to bit 15 / 31 */
+            for (int g = 0; g <= NL; g++) {
+                uint32_t hi = 0, lo = is_low(nu) ? 0x80u : 0u, c3 = 0, N = 0, A = 0;
+                if (g < NL) {
+                    const uint32_t H = __byte_perm(w[2 * g], w[2 * g + 1], 0x7531);    /* high bytes */
+                    const uint32_t Lo = __byte_perm(w[2 * g], w[2 * g + 1], 0x6420);   /* low bytes */
+                    const uint32_t hz = zero_bytes(H);
+                    const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;   /* >= 0x0800 */
+                    const uint32_t sur = zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);            /* D800-DFFF */
+                    const uint32_t t = H << 5;   /* bit 2 of each high byte (a low surrogate) to bit 7 */
                     hi = sur & ~t;
                     lo = sur & t;
-                    const uint32_t ph = __byte_perm(hprev, hi, 0x5432);   /* the unit before each unit is high */
+                    const uint32_t ph = __byte_perm(hprev, hi, 0x6543);   /* the unit before each unit is high */
                     if (VALIDATE) bad |= ph ^ lo;
                     hprev = hi;
-                    c2 = ge800 & ~sur;                  /* 3-byte unit */
-                    N = ~(lo & ph) & 0x80008000u;
-                    A = (ge80 ^ c2) & N;
+                    c3 = ge08 & ~sur;                   /* 3-byte unit */
+                    N = ~(lo & ph) & 0x80808080u;
+                    A = ~(hz & ~Lo) & ~c3 & N;         /* neither ASCII nor 3-byte */
                 }
-                if (k > 0) {   /* finish word k-1 */
-                    const uint32_t nl = __funnelshift_r(p_lo, lo, 16);   /* its units' next unit is low */
-                    const uint32_t B = p_c2 | (p_hi & nl);
-                    if ((k - 1) % 2 == 0) {
-                        q_N = p_N;
-                        q_A = p_A;
-                        q_B = B;
-                    } else {   /* bytes of units 4j .. 4j+3 from the flags at bits 15 / 31 of words 2j, 2j+1 */
-                        const uint32_t L = (__byte_perm(q_N, p_N, 0x7531) >> 7) +
-                                           (__byte_perm(q_A, p_A, 0x7531) >> 7) +
-                                           (__byte_perm(q_B, B, 0x7531) >> 6);
-                        n_len[(k - 1) / 2] = L;
-                        lens += L;
-                    }
+                if (g > 0) {   /* finish group g-1: the bytes of its four units */
+                    const uint32_t nl = __funnelshift_r(p_lo, lo, 8);   /* its units' next unit is low */
+                    const uint32_t B = p_c3 | (p_hi & nl);
+                    const uint32_t L = (p_N >> 7) + (p_A >> 7) + (B >> 6);
+                    n_len[g - 1] = L;
+                    lens += L;
                 }
-                p_c2 = c2;
+                p_c3 = c3;
                 p_hi = hi;
                 p_lo = lo;
                 p_N = N;

@@ -79,21 +79,6 @@ __device__ __forceinline__ uint32_t unit_of(uint32_t u) { return BE ? __byte_per
 __device__ __forceinline__ bool is_high(uint32_t u) { return (u & 0xFC00) == 0xD800; }
 __device__ __forceinline__ bool is_low(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
 
-/* Any unit of the two in x in D800-DFFF? */
-__device__ __forceinline__ bool has_surrogate(uint32_t x)
-{
-    const uint32_t y = (x & 0xF800F800u) ^ 0xD800D800u;   /* a zero half = surrogate */
-    return ((y - 0x00010001u) & ~y & 0x80008000u) != 0;
-}
-
-/* Bit 15 of each 16-bit half: set when the half of x is zero.  Exact for
- * halves that are multiples of 0x400 (a borrow out of a zero low half leaves
- * such a high half's bit 15 clear unless it is zero too). */
-__device__ __forceinline__ uint32_t zero_halves(uint32_t x)
-{
-    return (x - 0x00010001u) & ~x & 0x80008000u;
-}
-
 /* Bit 7 of each byte: set when that byte of x is zero (exact per byte: no
  * carry crosses a byte). */
 __device__ __forceinline__ uint32_t zero_bytes(uint32_t x)
@@ -645,18 +630,20 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
 template <int WORDS>
 __device__ __forceinline__ uint32_t surrogate_mismatch(const uint32_t (&w)[WORDS], uint32_t pu, uint32_t nu)
 {
+    static_assert(WORDS % 2 == 0, "four units per step");
     uint32_t bad = 0;
-    uint32_t hcarry = is_high(pu) ? 0x8000u : 0u;   /* "high" of the unit before, at bit 15 */
+    uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* byte 3: the unit before the group is high */
 #pragma unroll
-    for (int k = 0; k < WORDS; k++) {
-        const uint32_t x = (w[k] & 0xFC00FC00u) ^ 0xD800D800u;   /* zero half: high surrogate */
-        const uint32_t hi = zero_halves(x);
-        const uint32_t lo = zero_halves(x ^ 0x04000400u);        /* zero half: low surrogate */
-        /* bit 15: pair (2k-1, 2k); bit 31: pair (2k, 2k+1) */
-        bad |= ((hi << 16) | hcarry) ^ lo;
-        hcarry = hi >> 16;
+    for (int g = 0; g < WORDS / 2; g++) {
+        /* the high bytes of four units; flags at bit 7 of each byte */
+        const uint32_t H = __byte_perm(w[2 * g], w[2 * g + 1], 0x7531);
+        const uint32_t sur = zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
+        const uint32_t t = H << 5;   /* bit 2 of each high byte (a low surrogate) to bit 7 */
+        const uint32_t hi = sur & ~t, lo = sur & t;
+        bad |= __byte_perm(hprev, hi, 0x6543) ^ lo;   /* "the unit before is high" vs "this unit is low" */
+        hprev = hi;
     }
-    return bad | ((hcarry != 0) != is_low(nu));
+    return bad | ((hprev >> 31) != (is_low(nu) ? 1u : 0u));
 }
 
 template <int THREADS, int WORDS, bool BE>
@@ -721,9 +708,9 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
     reset_workspace(hdr, nullptr, 0);
 }
 
-/* UTF-8 length (Table 2): n + #(u >= 0x80) + #(u >= 0x800) - #surrogates, the
- * three counts taken two units at a time.  A unit outside the input reads as
- * zero and adds nothing. */
+/* UTF-8 length (Table 2): n + #(u >= 0x80) + #(u >= 0x800 and not a
+ * surrogate), the counts taken four units at a time on their gathered high
+ * and low bytes.  A unit outside the input reads as zero and adds nothing. */
 template <int THREADS, int WORDS, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tiles,
@@ -745,18 +732,17 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
         const uint64_t next = tile + gridDim.x;
         uint32_t v[WORDS];
         if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
-        uint32_t up = 0, sur = 0;   /* per-half counts in bits 0-15 and 16-31 */
+        uint32_t up = 0;   /* per-byte counts of the extra bytes, at most 2 per group */
 #pragma unroll
-        for (int k = 0; k < WORDS; k++) {
-            const uint32_t x = units_of<BE>(w[k]);
-            /* a half >= 0x80: one of bits 7-15 set; >= 0x800: one of bits 11-15 */
-            const uint32_t ge80 = (((x & 0x7F807F80u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-            const uint32_t ge800 = (((x & 0x78007800u) + 0x7FFF7FFFu) | x) & 0x80008000u;
-            const uint32_t s = zero_halves((x & 0xF800F800u) ^ 0xD800D800u);
-            up += (ge80 >> 15) + (ge800 >> 15);
-            sur += s >> 15;
+        for (int g = 0; g < WORDS / 2; g++) {
+            const uint32_t x0 = units_of<BE>(w[2 * g]), x1 = units_of<BE>(w[2 * g + 1]);
+            const uint32_t H = __byte_perm(x0, x1, 0x7531), Lo = __byte_perm(x0, x1, 0x6420);
+            const uint32_t ge80 = ~(zero_bytes(H) & ~Lo) & 0x80808080u;                 /* >= 0x0080 */
+            const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;   /* >= 0x0800 */
+            const uint32_t c3 = ge08 & ~zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);     /* and no surrogate */
+            up += (ge80 >> 7) + (c3 >> 7);
         }
-        acc += (up & 0xFFFF) + (up >> 16) - (sur & 0xFFFF) - (sur >> 16);
+        acc += byte_sum(up);
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];
         tile = next;

@@ -59,7 +59,6 @@ struct BatchShared {
     uint32_t warp_f[33];
     unsigned long long warp_v[33];
     unsigned long long lb_sum[32];
-    unsigned lb_has[32];
     unsigned long long carry;
 };
 
@@ -253,65 +252,57 @@ __device__ void block_seg_scan(bool f, uint64_t v, BatchShared &sm, bool *ef, ui
 }
 
 /* Segmented look-back: the sum carried into tile t from the string it
- * begins inside.  All threads; returns the value to every thread. */
+ * begins inside.  Warp 0 walks back 32 tiles at a time, waiting (bounded)
+ * for each status word, and stops at the nearest tile that published an
+ * inclusive prefix or holds a string start (usually the tile just before);
+ * the other warps only wait for the result.  Called by all threads; returns
+ * the value to every thread. */
 template <int THREADS>
 __device__ uint64_t block_seg_look_back(unsigned long long *status, long long tile, unsigned epoch,
                                         unsigned *flags, BatchShared &sm)
 {
-    constexpr int WARPS = THREADS / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t carry = 0;
-    long long end = tile - 1;
-    while (end >= 0) {
-        const long long idx = end - threadIdx.x;
-        bool stop = true;
-        uint64_t value = 0;
-        if (idx >= 0) {
-            int spins = 0;
-            unsigned ns = 32;
-            while (true) {
-                const uint64_t w = ld_acquire(status + idx);
-                const uint64_t fl = (w >> 40) & 3;
-                if ((unsigned)(w >> 43) == (epoch & SEG_EPOCH_MASK) && fl != 0) {
-                    stop = fl == ST_PREFIX || ((w >> 42) & 1);
-                    value = w & VALUE_MASK;
-                    break;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        uint64_t carry = 0;
+        long long end = tile - 1;
+        while (end >= 0) {
+            const long long idx = end - lane;
+            bool stop = true;
+            uint64_t value = 0;
+            if (idx >= 0) {
+                int spins = 0;
+                unsigned ns = 32;
+                while (true) {
+                    const uint64_t w = ld_acquire(status + idx);
+                    const uint64_t fl = (w >> 40) & 3;
+                    if ((unsigned)(w >> 43) == (epoch & SEG_EPOCH_MASK) && fl != 0) {
+                        stop = fl == ST_PREFIX || ((w >> 42) & 1);
+                        value = w & VALUE_MASK;
+                        break;
+                    }
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(flags, FLAG_TIMEOUT);
+                        stop = true;
+                        value = 0;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
                 }
-                if (++spins > SPIN_LIMIT) {
-                    atomicOr(flags, FLAG_TIMEOUT);
-                    stop = true;
-                    value = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
             }
-        }
-        const unsigned pmask = __ballot_sync(FULL_MASK, stop);
-        const int st = pmask ? __ffs(pmask) - 1 : 31;
-        uint64_t v = lane <= st ? value : 0;
+            const unsigned pmask = __ballot_sync(FULL_MASK, stop);
+            const int st = pmask ? __ffs(pmask) - 1 : 31;
+            uint64_t v = lane <= st ? value : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
-        if (lane == 0) {
-            sm.lb_sum[warp] = v;
-            sm.lb_has[warp] = pmask != 0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+            carry += v;
+            if (pmask) break;
+            end -= 32;
         }
-        __syncthreads();
-        uint64_t add = 0;
-        bool found = false;
-#pragma unroll
-        for (int k = 0; k < WARPS; k++) {
-            if (!found) {
-                add += sm.lb_sum[k];
-                found = sm.lb_has[k] != 0;
-            }
-        }
-        __syncthreads();
-        carry += add;
-        if (found) break;
-        end -= THREADS;
+        if (lane == 0) sm.lb_sum[0] = carry;
     }
-    return carry;
+    __syncthreads();
+    return sm.lb_sum[0];
 }
 
 /* ------------------------------------------------------------------------

@@ -413,6 +413,9 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                 const uint64_t m = block_min<THREADS>(cap_first, s_min);
                 if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
             }
+            /* this barrier also orders thread 0's ring entry for the tile
+             * now in flight (written by issue() above) before every thread
+             * reads it at the top of the next iteration */
             __syncthreads();
         }
 

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "utf16_scheme.h"
 
 namespace gputf {
 
@@ -78,13 +79,6 @@ __device__ __forceinline__ uint32_t unit_of(uint32_t u) { return BE ? __byte_per
 
 __device__ __forceinline__ bool is_high(uint32_t u) { return (u & 0xFC00) == 0xD800; }
 __device__ __forceinline__ bool is_low(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
-
-/* Bit 7 of each byte: set when that byte of x is zero (exact per byte: no
- * carry crosses a byte). */
-__device__ __forceinline__ uint32_t zero_bytes(uint32_t x)
-{
-    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
-}
 
 /* Sum of the four bytes of x (the sum below 256). */
 __device__ __forceinline__ uint32_t byte_sum(uint32_t x) { return (x * 0x01010101u) >> 24; }
@@ -308,48 +302,19 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             }
             const uint32_t pu = unit_of<BE>(sb[i0 - 1]), nu = unit_of<BE>(sb[i0 + UPT]);
             const long long e0 = (long long)(x0 + (uint64_t)tid * UPT);
-            /* bytes per unit (Table 2, with a surrogate pair written whole
-             * by its high unit): 1 below 0x80, 2 below 0x800, 3 for the rest
-             * of the BMP, 4 for a high unit followed by a low one, 0 for that
-             * low unit, and 2 for a lone surrogate, so no tile needs more than
-             * 3 bytes a unit (plus one for a pair cut by the tile's end).
-             * Four units per step: their high bytes (and low bytes) gathered
-             * into one word by a byte permute, classified with exact per-byte
-             * tests, as flags at bit 7 of each byte:
-             *   N: not the low half of a pair (counts 1),
-             *   A: counts one more (2-byte units and surrogates other than a
-             *      pair's low half),
-             *   B: counts two more (3-byte units and a pair's high half);
-             * a group's B needs the "next unit is low" flags of the group
-             * after it, so each group is finished one step later.  Section
-             * 3's pairing rule is checked as "the unit before is high" ==
-             * "this unit is low" for every two adjacent units. */
+            /* bytes per unit (utf16_scheme.h: Table 2, with a surrogate pair
+             * written whole by its high unit, so no tile needs more than 3
+             * bytes a unit, plus one for a pair cut by the tile's end), four
+             * units per step; Section 3's pairing rule checked on the way */
             uint32_t lens = 0, bad = 0;
-            uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* byte 3: the unit before the group is high */
+            uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;
             uint32_t p_c3 = 0, p_hi = 0, p_lo = 0, p_N = 0, p_A = 0;   /* the group before */
 #pragma unroll
             for (int g = 0; g <= NL; g++) {
-                uint32_t hi = 0, lo = is_low(nu) ? 0x80u : 0u, c3 = 0, N = 0, A = 0;
-                if (g < NL) {
-                    const uint32_t H = __byte_perm(w[2 * g], w[2 * g + 1], 0x7531);    /* high bytes */
-                    const uint32_t Lo = __byte_perm(w[2 * g], w[2 * g + 1], 0x6420);   /* low bytes */
-                    const uint32_t hz = zero_bytes(H);
-                    const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;   /* >= 0x0800 */
-                    const uint32_t sur = zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);            /* D800-DFFF */
-                    const uint32_t t = H << 5;   /* bit 2 of each high byte (a low surrogate) to bit 7 */
-                    hi = sur & ~t;
-                    lo = sur & t;
-                    const uint32_t ph = __byte_perm(hprev, hi, 0x6543);   /* the unit before each unit is high */
-                    if (VALIDATE) bad |= ph ^ lo;
-                    hprev = hi;
-                    c3 = ge08 & ~sur;                   /* 3-byte unit */
-                    N = ~(lo & ph) & 0x80808080u;
-                    A = ~(hz & ~Lo) & ~c3 & N;         /* neither ASCII nor 3-byte */
-                }
-                if (g > 0) {   /* finish group g-1: the bytes of its four units */
-                    const uint32_t nl = __funnelshift_r(p_lo, lo, 8);   /* its units' next unit is low */
-                    const uint32_t B = p_c3 | (p_hi & nl);
-                    const uint32_t L = (p_N >> 7) + (p_A >> 7) + (B >> 6);
+                uint32_t c3 = 0, hi = 0, lo = is_low(nu) ? 0x80u : 0u, N = 0, A = 0;
+                if (g < NL) gputf_u16_classify(w[2 * g], w[2 * g + 1], &hprev, &bad, &c3, &hi, &lo, &N, &A);
+                if (g > 0) {   /* finish group g-1 */
+                    const uint32_t L = gputf_u16_counts(p_c3, p_hi, p_lo, p_N, p_A, lo);
                     n_len[g - 1] = L;
                     lens += L;
                 }
@@ -359,7 +324,8 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 p_N = N;
                 p_A = A;
             }
-            if (VALIDATE) bad |= (uint32_t)((hprev >> 31) != (is_low(nu) ? 1u : 0u));
+            if (VALIDATE) bad |= gputf_u16_end_mismatch(hprev, nu);
+            else bad = 0;
             n_total = byte_sum(lens);
             uint32_t inr = 0xFFFFFFFFu;
             if (!interior) {   /* units outside the input write nothing */
@@ -640,7 +606,7 @@ __device__ __forceinline__ uint32_t surrogate_mismatch(const uint32_t (&w)[WORDS
     for (int g = 0; g < WORDS / 2; g++) {
         /* the high bytes of four units; flags at bit 7 of each byte */
         const uint32_t H = __byte_perm(w[2 * g], w[2 * g + 1], 0x7531);
-        const uint32_t sur = zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
+        const uint32_t sur = gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
         const uint32_t t = H << 5;   /* bit 2 of each high byte (a low surrogate) to bit 7 */
         const uint32_t hi = sur & ~t, lo = sur & t;
         bad |= __byte_perm(hprev, hi, 0x6543) ^ lo;   /* "the unit before is high" vs "this unit is low" */
@@ -740,9 +706,9 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
         for (int g = 0; g < WORDS / 2; g++) {
             const uint32_t x0 = units_of<BE>(w[2 * g]), x1 = units_of<BE>(w[2 * g + 1]);
             const uint32_t H = __byte_perm(x0, x1, 0x7531), Lo = __byte_perm(x0, x1, 0x6420);
-            const uint32_t ge80 = ~(zero_bytes(H) & ~Lo) & 0x80808080u;                 /* >= 0x0080 */
+            const uint32_t ge80 = ~(gputf_zero_bytes(H) & ~Lo) & 0x80808080u;                 /* >= 0x0080 */
             const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;   /* >= 0x0800 */
-            const uint32_t c3 = ge08 & ~zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);     /* and no surrogate */
+            const uint32_t c3 = ge08 & ~gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);     /* and no surrogate */
             up += (ge80 >> 7) + (c3 >> 7);
         }
         acc += byte_sum(up);

@@ -40,7 +40,9 @@ METRIC = "validated UTF-8<->UTF-16 input GB/s, % of HBM roofline; serving p99 la
 WORKLOAD = "utf16le_to_utf8_validating_256MiB_cjk70_ascii20_emoji10"
 KERNEL = "utf16_to_utf8_kernel"
 KERNEL_SOURCES = ["paper_2109_10433_gb300/csrc/utf16_to_utf8.cu",
-                  "paper_2109_10433_gb300/csrc/common.cuh"]
+                  "paper_2109_10433_gb300/csrc/common.cuh",
+                  "paper_2109_10433_gb300/csrc/utf16_scheme.h",
+                  "paper_2109_10433_gb300/csrc/utf8_scheme.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "utf16_to_utf8_256MiB_traffic.json")
 
 

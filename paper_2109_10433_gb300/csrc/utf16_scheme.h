@@ -30,22 +30,10 @@
 #define GPUTF_UTF16_SCHEME_H
 
 #include <stdint.h>
-#include "utf8_scheme.h"   /* GPUTF_HD, gputf_prmt, gputf_fshr */
+#include "utf8_scheme.h"   /* GPUTF_HD, gputf_bperm, gputf_fshr */
 
 GPUTF_HD int gputf_is_high(uint32_t u) { return (u & 0xFC00) == 0xD800; }
 GPUTF_HD int gputf_is_low(uint32_t u) { return (u & 0xFC00) == 0xDC00; }
-
-/* Byte permute with plain selectors (no sign-replicate mode): the compiler's
- * intrinsic on the GPU, which it can schedule and combine, the PTX model on
- * the host. */
-GPUTF_HD uint32_t gputf_bperm(uint32_t a, uint32_t b, uint32_t sel)
-{
-#if defined(__CUDA_ARCH__)
-    return __byte_perm(a, b, sel);
-#else
-    return gputf_prmt(a, b, sel);
-#endif
-}
 
 /* Bit 7 of each byte: set when that byte of x is zero (exact per byte: no
  * carry crosses a byte). */

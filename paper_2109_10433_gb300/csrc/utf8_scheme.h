@@ -89,6 +89,46 @@ GPUTF_HD uint32_t gputf_fshr(uint32_t lo, uint32_t hi, uint32_t s)
 #endif
 }
 
+/* Byte permute with plain selectors (no sign-replicate mode): the compiler's
+ * intrinsic on the GPU, which it can schedule and combine, the PTX model on
+ * the host. */
+GPUTF_HD uint32_t gputf_bperm(uint32_t a, uint32_t b, uint32_t sel)
+{
+#if defined(__CUDA_ARCH__)
+    return __byte_perm(a, b, sel);
+#else
+    return gputf_prmt(a, b, sel);
+#endif
+}
+
+/* x << s and x >> s for any s, 0 once s >= 32 (the GPU's clamped shifts). */
+GPUTF_HD uint32_t gputf_shl(uint32_t x, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_lc(0u, x, s);
+#else
+    return s >= 32 ? 0u : x << s;
+#endif
+}
+GPUTF_HD uint32_t gputf_shr(uint32_t x, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_rc(x, 0u, s);
+#else
+    return s >= 32 ? 0u : x >> s;
+#endif
+}
+
+/* Leading zero bits of x (32 for 0). */
+GPUTF_HD uint32_t gputf_clz(uint32_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return (uint32_t)__clz(x);
+#else
+    return x ? (uint32_t)__builtin_clz(x) : 32u;
+#endif
+}
+
 /* Pack the four nibbles held in the low halves of the bytes of x into a
  * 16-bit PRMT selector (nibble k = byte k); bits 16-31 are zero. */
 GPUTF_HD uint32_t gputf_pack_nibbles(uint32_t x)
@@ -244,5 +284,32 @@ GPUTF_HD uint64_t gputf_utf8_first_flag(const uint8_t *in, uint64_t n)
     return UINT64_MAX;
 }
 #endif
+
+/*
+ * UTF-16 of the character whose lead is byte 0 of q (bytes 1..3 follow);
+ * returns the unit count, *u0 and *u1 the units.  With the bytes in
+ * big-endian order, the sequence length n is the number of leading ones of
+ * the lead (taken as 1 for ASCII); shifting left and back by n clears the
+ * lead's prefix, masking with 3F clears the continuation prefixes, and two
+ * shift-and-mask steps pack the four 6-bit groups (Section 3; Figs. 2-4)
+ * into b0 << 18 | b1 << 12 | b2 << 6 | b3, whose top 6n bits are the scalar
+ * value.  Four-byte characters give v - 0x10000 split under 110110 / 110111
+ * (Fig. 4).  Any lead byte >= 0xF0 counts two units, as the length pass
+ * counts it; the units of an invalid sequence are unspecified.
+ */
+GPUTF_HD int gputf_utf8_decode(uint32_t q, uint32_t *u0, uint32_t *u1)
+{
+    const uint32_t r = gputf_bperm(q, 0u, 0x0123);   /* lead in bits 24-31 */
+    const uint32_t clo = gputf_clz(~r);
+    const uint32_t n = clo > 1 ? clo : 1u;
+    const uint32_t v = gputf_shr(gputf_shl(r, n), n) & 0x7F3F3F3Fu;
+    const uint32_t t = ((v >> 2) & 0x3FC03FC0u) | (v & 0x00FF00FFu);     /* two 12-bit halves */
+    const uint32_t code = gputf_shr(((t >> 4) & 0x0FFFF000u) | (t & 0xFFFu), 24u - 6u * n);
+    const uint32_t x = code - 0x10000u;
+    const int pair = n >= 4;
+    *u0 = pair ? (0xD800u | ((x >> 10) & 0x3FFu)) : code;
+    *u1 = 0xDC00u | (x & 0x3FFu);
+    return pair ? 2 : 1;
+}
 
 #endif

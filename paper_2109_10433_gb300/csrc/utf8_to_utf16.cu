@@ -94,31 +94,6 @@ __device__ __forceinline__ uint32_t range_mask(long long ex, uint64_t head, uint
 /* Byte index (0..3) of the lowest byte with bit 7 set in a nonzero mask. */
 __device__ __forceinline__ int first_byte(uint32_t m) { return (__ffs(m) - 8) >> 3; }
 
-/* UTF-16 of the character whose lead is byte 0 of q (bytes 1..3 follow).
- * Returns the unit count; *u0 and *u1 get the units.  With the bytes in
- * big-endian order, the sequence length n is the number of leading ones of
- * the lead (taken as 1 for ASCII); shifting left and back by n clears the
- * lead's prefix, masking with 3F clears the continuation prefixes, and two
- * shift-and-mask steps pack the four 6-bit groups (Section 3; Figs. 2-4)
- * into b0 << 18 | b1 << 12 | b2 << 6 | b3, of which the top 6n bits are the
- * scalar value.  Four-byte characters give v - 0x10000 split under 110110 /
- * 110111 (Fig. 4).  Any byte >= 0xF0 counts two units, as the length pass
- * counts it. */
-__device__ __forceinline__ int decode_utf8(uint32_t q, uint32_t *u0, uint32_t *u1)
-{
-    const uint32_t r = __byte_perm(q, 0u, 0x0123);   /* lead in bits 24-31 */
-    const uint32_t clo = __clz(~r);
-    const uint32_t n = clo > 1 ? clo : 1u;
-    const uint32_t v = ((r << n) >> n) & 0x7F3F3F3Fu;
-    const uint32_t t = ((v >> 2) & 0x3FC03FC0u) | (v & 0x00FF00FFu);     /* two 12-bit halves */
-    const uint32_t code = (((t >> 4) & 0x0FFFF000u) | (t & 0xFFFu)) >> (24 - 6 * n);
-    const uint32_t x = code - 0x10000;
-    const bool pair = n >= 4;
-    *u0 = pair ? (0xD800 | ((x >> 10) & 0x3FF)) : code;
-    *u1 = 0xDC00 | (x & 0x3FF);
-    return pair ? 2 : 1;
-}
-
 constexpr int HALO8 = 16;   /* bytes staged on each side of a tile */
 
 template <int THREADS, int WORDS, int STAGES>
@@ -322,7 +297,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     lm &= lm - 1;
                     const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + (p & ~3));
                     uint32_t u0, u1;
-                    const int c = decode_utf8(__funnelshift_r(wp[0], wp[1], 8 * (p & 3)), &u0, &u1);
+                    const int c = gputf_utf8_decode(__funnelshift_r(wp[0], wp[1], 8 * (p & 3)), &u0, &u1);
                     out16[o] = (uint16_t)u0;
                     if (c == 2) out16[o + 1] = (uint16_t)u1;
                     o += c;

@@ -137,74 +137,6 @@ __device__ __forceinline__ uint64_t look_back(unsigned long long *status, long l
     return exclusive;
 }
 
-/*
- * Exclusive prefix of tile `tile` by decoupled look-back with a window as wide
- * as the block: every thread polls one predecessor, so one round trip to L2
- * covers THREADS tiles.  With a persistent grid, hundreds of tiles are in
- * flight at once and the nearest inclusive prefix is often more than a warp's
- * width back; a narrow window would need one round trip per 32 tiles.
- * Called by all threads of the block (uniform `tile`); returns the prefix to
- * every thread.  `s_sum` and `s_has` hold THREADS/32 entries each.
- */
-template <int THREADS>
-__device__ __forceinline__ uint64_t block_look_back(unsigned long long *status, long long tile,
-                                                    unsigned epoch, unsigned *flags,
-                                                    unsigned long long *s_sum, unsigned *s_has)
-{
-    constexpr int WARPS = THREADS / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t exclusive = 0;
-    long long end = tile - 1;
-    while (end >= 0) {
-        const long long idx = end - threadIdx.x;
-        uint64_t flag = ST_PREFIX, value = 0;
-        if (idx >= 0) {
-            int spins = 0;
-            unsigned ns = 32;
-            while (true) {
-                const uint64_t w = ld_acquire(status + idx);
-                if ((unsigned)(w >> 43) == epoch && ((w >> 40) & 3) != 0) {
-                    flag = (w >> 40) & 3;
-                    value = w & VALUE_MASK;
-                    break;
-                }
-                if (++spins > SPIN_LIMIT) {
-                    atomicOr(flags, FLAG_TIMEOUT);
-                    flag = ST_PREFIX;
-                    value = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
-            }
-        }
-        const unsigned pmask = __ballot_sync(FULL_MASK, flag == ST_PREFIX);
-        const int stop = pmask ? __ffs(pmask) - 1 : 31;
-        uint64_t v = lane <= stop ? value : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
-        if (lane == 0) {
-            s_sum[warp] = v;
-            s_has[warp] = pmask != 0;
-        }
-        __syncthreads();
-        uint64_t add = 0;
-        bool found = false;
-#pragma unroll
-        for (int w = 0; w < WARPS; w++) {
-            if (!found) {
-                add += s_sum[w];
-                found = s_has[w] != 0;
-            }
-        }
-        __syncthreads();
-        exclusive += add;
-        if (found) break;
-        end -= THREADS;
-    }
-    return exclusive;
-}
-
 /* Inclusive warp scan of 32-bit values. */
 __device__ __forceinline__ uint32_t warp_inclusive(uint32_t v)
 {

@@ -1,27 +1,26 @@
 /*
- * Validating UTF-16LE -> UTF-8, and the UTF-16 validate-only and length-only
- * passes.
+ * Validating UTF-16LE (or UTF-16BE) -> UTF-8, and the UTF-16 validate-only
+ * and length-only passes.
  *
- * One CTA transcodes one tile of TILE input units (tiles in ticket order):
- *   1. load: each thread reads UPT consecutive units with aligned 16-byte
- *      loads (the tile grid is aligned to 16 bytes below the input pointer),
- *      plus the unit before and the unit after its chunk from the
- *      neighbouring lanes or, at warp edges, from memory;
- *   2. validate (Section 3): a high surrogate D800-DBFF must be followed by a
- *      low surrogate DC00-DFFF and a low surrogate must follow a high one;
- *      threads whose units hold no surrogate skip the check (it cannot fail
- *      there), as the paper only validates where surrogates appear;
- *   3. per-unit output length (Section 5's four cases): 1 byte below 0x80,
- *      2 below 0x800, 3 for the rest of the BMP, and 2 for each surrogate
- *      unit, so that a pair yields its 4 bytes; summed per thread, scanned
- *      over the block and over earlier tiles by decoupled look-back;
- *   4. encode each unit (lead prefixes 110 / 1110 / 11110 and continuation
- *      prefix 10 over 5/4/3 + 6-bit groups): the high unit of a pair emits
- *      the first two bytes of the character (F0 | c >> 18, 80 | c >> 12 & 3F,
- *      with c >> 10 = (high & 0x3FF) + 0x40) and the low unit the last two,
- *      so every unit writes independently.  Each thread packs its bytes into
- *      32-bit words of a shared-memory staging buffer aligned like the
- *      output, then the tile's range is written with aligned 16-byte stores;
+ * The transcoder is a persistent kernel; each CTA takes tiles of 6144 units
+ * in ticket order and, for each:
+ *   1. load: the tile (plus 8 units of halo on each side) arrives in a
+ *      two-stage shared-memory ring by a TMA bulk copy; each thread reads
+ *      its 24 consecutive units, the unit before and the unit after;
+ *   2. per-unit output bytes and validation (utf16_scheme.h, Section 3 and
+ *      Table 2), four units per step on their gathered high bytes: 1, 2 or
+ *      3 bytes by value, the 4 bytes of a surrogate pair on its high unit and
+ *      none on its low unit, 2 for a lone surrogate; the pairing rule is
+ *      checked on the way;
+ *   3. offsets: a block scan of the per-thread sums and a decoupled
+ *      look-back over earlier tiles (warp 0 alone);
+ *   4. encode each unit (lead prefixes 110 / 1110 / 11110, continuation
+ *      prefix 10 over 6-bit groups; Section 5) into a shared-memory staging
+ *      buffer at tile-local offsets: warps whose units all take one length
+ *      store at fixed offsets; otherwise each thread writes its units back to
+ *      front, three unconditional continuation-byte stores and one predicated
+ *      lead store per unit; the tile's range then goes out with aligned
+ *      16-byte stores, realigned by funnel shifts;
  *   5. the first invalid unit (exact: no fix-up is needed in UTF-16) goes to
  *      an atomicMin; the CTA that finishes last writes the result.
  */

@@ -1,13 +1,14 @@
 /*
- * Validating UTF-8 -> UTF-16LE, and the UTF-8 validate-only and length-only
- * passes.
+ * Validating UTF-8 -> UTF-16LE (or UTF-16BE), and the UTF-8 validate-only and
+ * length-only passes.
  *
- * One CTA transcodes one tile of TILE input bytes (tiles in ticket order):
- *   1. load: each thread reads BPT consecutive bytes with 16-byte loads (the
- *      tile grid is aligned to 16 bytes below the input pointer, so every
- *      load is aligned; the first and last chunk of the buffer are read byte
- *      by byte), plus the 4 bytes before its chunk and the 4 after, taken
- *      from the neighbouring lanes or, at warp edges, from memory;
+ * The transcoder is a persistent kernel; each CTA takes tiles of 8 KiB in
+ * ticket order and, for each:
+ *   1. load: the tile (plus 16 bytes of halo on each side) arrives in a
+ *      two-stage shared-memory ring by a TMA bulk copy (the tile grid is
+ *      aligned to 16 bytes below the input pointer; tiles at the ends of the
+ *      buffer are filled with guarded loads); each thread reads its 32
+ *      consecutive bytes and the 4 bytes before them;
  *   2. classify and validate: a warp whose bytes (and the bytes just before)
  *      are all ASCII skips validation (the all-ASCII fast path of
  *      Algorithm 3); other threads run the nibble-table scheme of
@@ -15,13 +16,13 @@
  *   3. per-byte output length: 1 unit at every byte that is not a
  *      continuation byte, 2 at a four-byte lead (Table 2: supplementary
  *      characters take a surrogate pair), summed per thread, scanned over the
- *      block and over all earlier tiles by decoupled look-back;
+ *      block and over all earlier tiles by decoupled look-back (warp 0);
  *   4. decode at every lead with the bit arithmetic of Section 3 and Figs.
- *      2-4 (payload bits of the lead and continuation bytes; for four-byte
- *      characters subtract 0x10000 and split into 110110 / 110111 halves),
- *      into a shared-memory staging buffer placed so that it shares the
- *      output's alignment, then write the tile's output range with aligned
- *      16-byte stores;
+ *      2-4 (gputf_utf8_decode in utf8_scheme.h; for four-byte characters
+ *      subtract 0x10000 and split into 110110 / 110111 halves) into a
+ *      shared-memory staging buffer at tile-local offsets, then write the
+ *      tile's output range with aligned 16-byte stores, realigned by funnel
+ *      shifts;
  *   5. the first flagged byte goes to an atomicMin; the CTA that finishes
  *      last turns it into the exact error start and class (scalar step of
  *      utf8_scheme.h), the output count of the valid prefix and the result.

@@ -1,5 +1,5 @@
 /*
- * gputf: validating UTF-8 <-> UTF-16LE transcoding on NVIDIA GB300 (sm_103a).
+ * gputf: validating UTF-8 <-> UTF-16 transcoding on NVIDIA GB300 (sm_103a).
  *
  * The problem is the one stated by Lemire & Mula, "Transcoding Billions of
  * Unicode Characters per Second with SIMD Instructions" (arXiv 2109.10433):
@@ -11,8 +11,9 @@
  *
  * Conventions shared by every call:
  *   - Units.  Sizes and positions count code units of the encoding they refer
- *     to: bytes for UTF-8, 16-bit units for UTF-16.  UTF-16 is little-endian;
- *     no byte-order mark is detected or removed (U+FEFF is an ordinary
+ *     to: bytes for UTF-8, 16-bit units for UTF-16.  UTF-16 is little-endian
+ *     except in the calls named utf16be, which take big-endian units; no
+ *     byte-order mark is detected or removed (U+FEFF is an ordinary
  *     character), and U+0000 is an ordinary character.
  *   - Memory.  `in`, `out`, the workspace and `res`/`len` are memory the
  *     caller owns: device memory (for example from torch.empty on a CUDA

@@ -567,7 +567,8 @@ def run_passes(args):
     UTF-16 input: the 256 MiB headline buffer (larger than L2).  UTF-8 input:
     64 MiB of the 4-byte-heavy mix (40% U+10000-10FFFF, 30% U+0800-FFFF,
     30% ASCII), valid; L2 is flushed (a 512 MB write) before every timed
-    launch."""
+    launch; and the 1 MiB Latin/Cyrillic buffer (90% U+0020-007E, 10%
+    U+0400-04FF), which stays in L2 (not flushed): a launch-bound case."""
     import torch
 
     import paper_2109_10433_gb300 as g
@@ -583,6 +584,9 @@ def run_passes(args):
     d16 = torch.from_numpy(u16.view(np.int16).copy()).cuda()
     d8 = torch.from_numpy(u8.copy()).cuda()
     n16, n8 = int(u16.size), int(u8.size)
+    u8s = W.latin_cyrillic_utf8_1mib()
+    d8s = torch.from_numpy(u8s.copy()).cuda()
+    n8s = int(u8s.size)
     # script-uniform UTF-16 text of the same size: all U+4E00-9FFF, all ASCII
     cjk = torch.from_numpy(W.utf16_text(5, n16, W.SCRIPT_CJK).view(np.int16).copy()).cuda()
     asc = torch.from_numpy(W.utf16_text(6, n16, W.SCRIPT_ASCII).view(np.int16).copy()).cuda()
@@ -594,6 +598,10 @@ def run_passes(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     len8 = g.utf8_length_from_utf16(d16, ws=ws)
     len16 = g.utf16_length_from_utf8(d8, ws=ws)
+    len16s = g.utf16_length_from_utf8(d8s, ws=ws)
+    inputs = {"utf16": ("utf16 %d MiB cjk/emoji" % args.mib, 2 * n16),
+              "utf8": ("utf8 64 MiB four-byte-heavy", n8),
+              "utf8_l2": ("utf8 1 MiB latin/cyrillic, L2-resident", n8s)}
     cases = [
         ("utf16_to_utf8", "utf16", lambda: L.gputf_utf16_to_utf8(g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr,
                                                                  ws.nbytes, g._ptr(res), sp), 2 * n16 + len8),
@@ -615,6 +623,8 @@ def run_passes(args):
          n8),
         ("utf16_length_from_utf8", "utf8", lambda: L.gputf_utf16_length_from_utf8(g._ptr(d8), n8, ws.ptr, ws.nbytes,
                                                                                    g._ptr(ln), sp), n8),
+        ("utf8_to_utf16 1 MiB", "utf8_l2", lambda: L.gputf_utf8_to_utf16(g._ptr(d8s), n8s, g._ptr(out16), n8s, ws.ptr,
+                                                                         ws.nbytes, g._ptr(res), sp), n8s + 2 * len16s),
     ]
     rows = []
     clocks = ClockSampler(None)
@@ -636,10 +646,10 @@ def run_passes(args):
             ms.append(e0.elapsed_time(e1))
         us = statistics.median(ms) * 1e3
         gbs = algo / (us * 1e-6) / 1e9
-        rows.append({"kernel": name, "input": "utf16 %d MiB cjk/emoji" % args.mib if src == "utf16"
-                     else "utf8 64 MiB four-byte-heavy", "input_bytes": (2 * n16 if src == "utf16" else n8),
+        desc, in_bytes = inputs[src]
+        rows.append({"kernel": name, "input": desc, "input_bytes": in_bytes,
                      "algorithmic_bytes": int(algo), "median_us": us, "min_us": min(ms) * 1e3,
-                     "input_gbs": (2 * n16 if src == "utf16" else n8) / (us * 1e-6) / 1e9,
+                     "input_gbs": in_bytes / (us * 1e-6) / 1e9,
                      "achieved_gbs": gbs, "frac": gbs / peak})
     clk = clocks.stop()
     print(json.dumps({"metric": "per-kernel algorithmic GB/s vs HBM roofline", "unit": "GB/s",

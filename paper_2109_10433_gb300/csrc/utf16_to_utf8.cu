@@ -474,23 +474,32 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
             uint8_t *gbase = out + G0 - shift;      /* 16-byte aligned; byte j <-> staging byte j - shift */
             const uint32_t lim = shift + (uint32_t)cnt;
-            const uint32_t nvec = (lim + 15) / 16;
+            const uint32_t vf = shift ? 1u : 0u, vl = lim >> 4;   /* the whole vectors: [vf, vl) */
             const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
-            for (uint32_t i = tid; i < nvec; i += THREADS) {
-                const uint32_t lo = 16 * i, hi = lo + 16;
-                if (lo >= shift && hi <= lim) {
+            if (r8 == 0) {
+                for (uint32_t i = vf + tid; i < vl; i += THREADS) {
                     const uint32_t j = 4 * i - q;
-                    uint4 ov;
-                    if (r8 == 0) {
-                        ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
-                    } else {
-                        const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
-                        ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
-                                        __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
-                    }
-                    st_stream16(gbase + lo, ov);
-                } else {
-                    for (uint32_t b = lo < shift ? shift : lo; b < (hi < lim ? hi : lim); b++) gbase[b] = outb[b - shift];
+                    st_stream16(gbase + 16 * i, make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]));
+                }
+            } else {
+                for (uint32_t i = vf + tid; i < vl; i += THREADS) {
+                    const uint32_t j = 4 * i - q;   /* >= 1: vf = 1 */
+                    const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
+                    st_stream16(gbase + 16 * i,
+                                make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
+                                           __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8)));
+                }
+            }
+            {   /* the partial vectors at the two ends, a byte per thread of the last warp */
+                const uint32_t head_end = 16 * vf < lim ? 16 * vf : lim;         /* bytes [shift, head_end) */
+                const uint32_t tail_start = 16 * vl > head_end ? 16 * vl : head_end;   /* [tail_start, lim) */
+                const int t = tid - (THREADS - 32);
+                if (t >= 0 && t < 16) {
+                    const uint32_t b = shift + (uint32_t)t;
+                    if (b < head_end) gbase[b] = outb[b - shift];
+                } else if (t >= 16) {
+                    const uint32_t b = tail_start + (uint32_t)(t - 16);
+                    if (b < lim) gbase[b] = outb[b - shift];
                 }
             }
 

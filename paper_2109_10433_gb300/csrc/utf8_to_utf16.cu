@@ -341,32 +341,41 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
             uint8_t *gbase = reinterpret_cast<uint8_t *>(out + G0) - shift;
             const uint32_t lim = shift + 2 * (uint32_t)cnt;
-            const uint32_t nvec = (lim + 15) / 16;
+            const uint32_t vf = shift ? 1u : 0u, vl = lim >> 4;   /* the whole vectors: [vf, vl) */
             const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
-            for (uint32_t i = tid; i < nvec; i += THREADS) {
-                const uint32_t lo = 16 * i, hi = lo + 16;
-                if (lo >= shift && hi <= lim) {
-                    const uint32_t j = 4 * i - q;
-                    uint4 ov;
-                    if (r8 == 0) {
-                        ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
-                    } else {
-                        const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
-                        ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
-                                        __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
-                    }
-                    if (BE) {   /* UTF-16BE: each unit's two bytes the other way round (shift is even) */
-                        ov.x = __byte_perm(ov.x, 0u, 0x2301);
-                        ov.y = __byte_perm(ov.y, 0u, 0x2301);
-                        ov.z = __byte_perm(ov.z, 0u, 0x2301);
-                        ov.w = __byte_perm(ov.w, 0u, 0x2301);
-                    }
-                    st_stream16(gbase + lo, ov);
-                } else {
-                    for (uint32_t b = (lo < shift ? shift : lo); b < (hi < lim ? hi : lim); b += 2) {
-                        const uint32_t u = *reinterpret_cast<const uint16_t *>(outb + b - shift);
-                        *reinterpret_cast<uint16_t *>(gbase + b) = (uint16_t)(BE ? __byte_perm(u, 0u, 0x4401) : u);
-                    }
+            for (uint32_t i = vf + tid; i < vl; i += THREADS) {
+                const uint32_t j = 4 * i - q;
+                uint4 ov;
+                if (r8 == 0) {
+                    ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
+                } else {   /* j >= 1: vf = 1 */
+                    const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
+                    ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
+                                    __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
+                }
+                if (BE) {   /* UTF-16BE: each unit's two bytes the other way round (shift is even) */
+                    ov.x = __byte_perm(ov.x, 0u, 0x2301);
+                    ov.y = __byte_perm(ov.y, 0u, 0x2301);
+                    ov.z = __byte_perm(ov.z, 0u, 0x2301);
+                    ov.w = __byte_perm(ov.w, 0u, 0x2301);
+                }
+                st_stream16(gbase + 16 * i, ov);
+            }
+            {   /* the partial vectors at the two ends, a unit per thread of the last warp */
+                const uint32_t head_end = 16 * vf < lim ? 16 * vf : lim;         /* bytes [shift, head_end) */
+                const uint32_t tail_start = 16 * vl > head_end ? 16 * vl : head_end;   /* [tail_start, lim) */
+                const int t = tid - (THREADS - 32);
+                uint32_t b = ~0u;
+                if (t >= 0 && t < 8) {
+                    b = shift + 2 * (uint32_t)t;
+                    if (b >= head_end) b = ~0u;
+                } else if (t >= 8 && t < 16) {
+                    b = tail_start + 2 * (uint32_t)(t - 8);
+                    if (b >= lim) b = ~0u;
+                }
+                if (b != ~0u) {
+                    const uint32_t u = *reinterpret_cast<const uint16_t *>(outb + b - shift);
+                    *reinterpret_cast<uint16_t *>(gbase + b) = (uint16_t)(BE ? __byte_perm(u, 0u, 0x4401) : u);
                 }
             }
 

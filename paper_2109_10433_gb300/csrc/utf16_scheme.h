@@ -86,4 +86,30 @@ GPUTF_HD uint32_t gputf_u16_end_mismatch(uint32_t hprev, uint32_t nu)
     return (hprev >> 31) ^ (gputf_is_low(nu) ? 1u : 0u);
 }
 
+/* The validate-only pass: the pairing check of four units (w0, w1 as for
+ * gputf_u16_classify), nonzero when two adjacent units break the rule;
+ * *hprev carries the "unit before is high" flag as there. */
+GPUTF_HD uint32_t gputf_u16_mismatch4(uint32_t w0, uint32_t w1, uint32_t *hprev)
+{
+    const uint32_t H = gputf_bperm(w0, w1, 0x7531);
+    const uint32_t sur = gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
+    const uint32_t t = H << 5;
+    const uint32_t hi = sur & ~t, lo = sur & t;
+    const uint32_t bad = gputf_bperm(*hprev, hi, 0x6543) ^ lo;
+    *hprev = hi;
+    return bad;
+}
+
+/* The length-only pass (Table 2's closed form, no pairing): for each of four
+ * units a byte holding its UTF-8 length minus one, [u >= U+0080] + [u >=
+ * U+0800 and not a surrogate], so that a surrogate unit counts 2 bytes. */
+GPUTF_HD uint32_t gputf_u16_utf8_extra4(uint32_t w0, uint32_t w1)
+{
+    const uint32_t H = gputf_bperm(w0, w1, 0x7531), Lo = gputf_bperm(w0, w1, 0x6420);
+    const uint32_t ge80 = ~(gputf_zero_bytes(H) & ~Lo) & 0x80808080u;                  /* >= U+0080 */
+    const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;     /* >= U+0800 */
+    const uint32_t c3 = ge08 & ~gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);   /* and no surrogate */
+    return (ge80 >> 7) + (c3 >> 7);
+}
+
 #endif

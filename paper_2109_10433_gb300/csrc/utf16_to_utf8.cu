@@ -611,16 +611,8 @@ __device__ __forceinline__ uint32_t surrogate_mismatch(const uint32_t (&w)[WORDS
     uint32_t bad = 0;
     uint32_t hprev = is_high(pu) ? 0x80000000u : 0u;   /* byte 3: the unit before the group is high */
 #pragma unroll
-    for (int g = 0; g < WORDS / 2; g++) {
-        /* the high bytes of four units; flags at bit 7 of each byte */
-        const uint32_t H = __byte_perm(w[2 * g], w[2 * g + 1], 0x7531);
-        const uint32_t sur = gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
-        const uint32_t t = H << 5;   /* bit 2 of each high byte (a low surrogate) to bit 7 */
-        const uint32_t hi = sur & ~t, lo = sur & t;
-        bad |= __byte_perm(hprev, hi, 0x6543) ^ lo;   /* "the unit before is high" vs "this unit is low" */
-        hprev = hi;
-    }
-    return bad | ((hprev >> 31) != (is_low(nu) ? 1u : 0u));
+    for (int g = 0; g < WORDS / 2; g++) bad |= gputf_u16_mismatch4(w[2 * g], w[2 * g + 1], &hprev);
+    return bad | gputf_u16_end_mismatch(hprev, nu);
 }
 
 template <int THREADS, int WORDS, bool BE>
@@ -711,14 +703,8 @@ utf8_length_from_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint6
         if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
         uint32_t up = 0;   /* per-byte counts of the extra bytes, at most 2 per group */
 #pragma unroll
-        for (int g = 0; g < WORDS / 2; g++) {
-            const uint32_t x0 = units_of<BE>(w[2 * g]), x1 = units_of<BE>(w[2 * g + 1]);
-            const uint32_t H = __byte_perm(x0, x1, 0x7531), Lo = __byte_perm(x0, x1, 0x6420);
-            const uint32_t ge80 = ~(gputf_zero_bytes(H) & ~Lo) & 0x80808080u;                 /* >= 0x0080 */
-            const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;   /* >= 0x0800 */
-            const uint32_t c3 = ge08 & ~gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);     /* and no surrogate */
-            up += (ge80 >> 7) + (c3 >> 7);
-        }
+        for (int g = 0; g < WORDS / 2; g++)
+            up += gputf_u16_utf8_extra4(units_of<BE>(w[2 * g]), units_of<BE>(w[2 * g + 1]));
         acc += byte_sum(up);
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];

@@ -18,7 +18,12 @@
  *   3. the pairing flag is set exactly when two adjacent units of
  *      pu, u[0..n), nu break the rule of Section 3; when pu is no low
  *      surrogate and nu no high one, exactly when the oracle finds the
- *      sequence pu, u, nu invalid.
+ *      sequence pu, u, nu invalid;
+ *   4. the validate-only pass's check (gputf_u16_mismatch4 over the groups,
+ *      then gputf_u16_end_mismatch) gives the same flag;
+ *   5. the length-only pass's count (n plus the bytes of
+ *      gputf_u16_utf8_extra4 over the groups) equals the oracle's UTF-8
+ *      length of u[0..n).
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -90,6 +95,19 @@ static int check_chunk(const uint16_t *u, int n, uint32_t pu, uint32_t nu)
         oracle_validate_utf16(ext, (uint64_t)n + 2, &r);
         if ((r.error != 0) != broken) return 3;
     }
+    /* 4, 5: the validate-only and length-only passes */
+    uint32_t vbad = 0, vprev = gputf_is_high(pu) ? 0x80000000u : 0u;
+    uint64_t len = (uint64_t)n;
+    for (int g = 0; g < n / 4; g++) {
+        const uint32_t w0 = u[4 * g] | ((uint32_t)u[4 * g + 1] << 16);
+        const uint32_t w1 = u[4 * g + 2] | ((uint32_t)u[4 * g + 3] << 16);
+        vbad |= gputf_u16_mismatch4(w0, w1, &vprev);
+        const uint32_t e = gputf_u16_utf8_extra4(w0, w1);
+        len += (e & 0xFF) + ((e >> 8) & 0xFF) + ((e >> 16) & 0xFF) + (e >> 24);
+    }
+    vbad |= gputf_u16_end_mismatch(vprev, nu);
+    if ((vbad != 0) != broken) return 4;
+    if (len != oracle_utf8_length_from_utf16(u, (uint64_t)n)) return 5;
     return 0;
 }
 

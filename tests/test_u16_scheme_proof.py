@@ -8,7 +8,9 @@ and a unit after (the kernel's thread chunk and its neighbours): prefix sums
 of the counts against the oracle's UTF-8 lengths at every split that does
 not cut a surrogate pair, the per-unit bounds that make the kernel's staging
 buffer big enough, and the pairing flag against the rule of Section 3 and
-the oracle's validator.  Domains:
+the oracle's validator; and the same header's arithmetic of the validate-only
+and length-only UTF-16 passes (pairing flag, and UTF-8 length against the
+oracle's).  Domains:
   - every 16-bit value at every position of a 24-unit chunk, the other units
     drawn from a set holding every class boundary;
   - every combination of boundary values over the five units around a group

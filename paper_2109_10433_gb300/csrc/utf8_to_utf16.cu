@@ -112,11 +112,25 @@ struct U8Layout {
  * the UTF-16 -> UTF-8 kernel): each iteration runs phase A of the tile n
  * whose input just arrived (lengths, validation, block scan, aggregate) and
  * phase B of the tile c before it (decode into the staging buffer,
- * look-back, inclusive prefix, write-out); as soon as the decoding has read
- * c's stage, a new ticket is taken and its input copy starts into that stage
- * (a two-stage ring).  Input arrives with 16 bytes of halo on each side: the
- * 3 bytes before a position validate it, the 3 after complete a character
- * that starts near the tile's end.
+ * look-back, inclusive prefix, write-out).  Thread 0 takes a new ticket as
+ * phase B starts and writes it to c's ring entry before the look-back
+ * barrier; after that barrier (every thread has read c's stage) the ticket's
+ * input copy starts into that stage (a two-stage ring).  Input arrives with
+ * 16 bytes of halo on each side: the 3 bytes before a position validate it,
+ * the 3 after complete a character that starts near the tile's end.
+ *
+ * Barriers per iteration: the block scan's two and the look-back barrier,
+ * and a last one only when no tile follows.  The ring entry is read at the
+ * top of the next iteration after the look-back barrier that follows its
+ * write; the staging buffer, the G0 word and the scan and minimum scratch
+ * words of this iteration are read before the next iteration's block scan,
+ * whose barriers come before anything rewrites them.  Without a next tile
+ * there is no scan, hence the last barrier.
+ *
+ * A look-back waits only for the aggregates of smaller tickets, and the
+ * ticket a CTA holds unpublished during its look-back is larger than the
+ * tile it looks back from, so the CTA holding the smallest unpublished
+ * ticket never waits: every wait ends.
  */
 template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
@@ -148,8 +162,8 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     const uint64_t endx = head + n;    /* extended index of the end position */
     const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
 
+    /* thread 0: put tile t (already in stage s's ring entry) in flight into stage s */
     auto issue = [&](unsigned long long t, int s) {
-        s_ring[s] = t;
         if (t >= tiles) return;
         const uint64_t x0 = t * TILE;
         if (x0 >= head + HALO8 && x0 + TILE + HALO8 <= endx) {
@@ -164,8 +178,11 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
-        issue(atomicAdd(&hdr->ticket, 1ull), 0);
-        issue(atomicAdd(&hdr->ticket, 1ull), 1);
+        for (int s = 0; s < STAGES; s++) {
+            const unsigned long long t0 = atomicAdd(&hdr->ticket, 1ull);
+            s_ring[s] = t0;
+            issue(t0, s);
+        }
     }
     __syncthreads();
 
@@ -256,6 +273,8 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * BPT);
             const long long lb_idx = (long long)c_tile - 1 - tid;   /* warp 0's lanes */
             const uint64_t lb_word = (tid < 32 && c_tile > 0 && lb_idx >= 0) ? ld_relaxed(status + lb_idx) : 0;
+            unsigned long long tk = 0;   /* the next tile's ticket (thread 0; its latency hides behind the decoding) */
+            if (tid == 0 && have_n) tk = atomicAdd(&hdr->ticket, 1ull);
 
             uint32_t w[WORDS];
 #pragma unroll
@@ -328,12 +347,13 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     st_release(status + c_tile, make_status(epoch, ST_PREFIX, v + c_total));
                 }
             }
+            if (tid == 0 && have_n) s_ring[c_stage] = tk;
             __syncthreads();
             const uint64_t G0 = c_tile > 0 ? s_lb_g0 : 0;
-            /* every thread has read c's stage: a new ticket's tile goes in
-             * flight into it (a ticket taken this late keeps the tiles in
-             * flight close together, so look-backs seldom wait) */
-            if (tid == 0 && have_n) issue(atomicAdd(&hdr->ticket, 1ull), c_stage);
+            const unsigned long long next_t = s_ring[c_stage];
+            /* every thread has read c's stage: the new ticket's tile goes in
+             * flight into it */
+            if (tid == 0 && have_n) issue(tk, c_stage);
 
             /* write the tile's units [G0, G0 + cnt), clipped to the capacity,
              * with aligned 16-byte stores assembled by funnel shifts */
@@ -398,10 +418,10 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                 const uint64_t m = block_min<THREADS>(cap_first, s_min);
                 if (tid == 0 && m != NONE) atomicMin(&hdr->cap_pos, (unsigned long long)m);
             }
-            /* this barrier also orders thread 0's ring entry for the tile
-             * now in flight (written by issue() above) before every thread
-             * reads it at the top of the next iteration */
-            __syncthreads();
+            /* with no tile to follow, the next iteration has no block scan:
+             * this barrier keeps the staging buffer and G0 until every thread
+             * has written its part out */
+            if (!have_n || next_t >= tiles) __syncthreads();
         }
 
         if (!have_n) break;

@@ -85,7 +85,7 @@ uint64_t scheme_check(const uint8_t *data, const uint64_t *offsets, uint64_t cou
     return total;
 }
 
-/* The scheme's verdict alone, for reporting. */
+/* The scheme's result alone, for reporting. */
 void scheme_one(const uint8_t *in, uint64_t n, int *cls, uint64_t *pos, uint64_t *flag)
 {
     *flag = gputf_utf8_first_flag(in, n);

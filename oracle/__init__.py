@@ -1,4 +1,5 @@
-"""Scalar CPU oracle for validating UTF-8 <-> UTF-16LE transcoding.
+"""Scalar CPU oracle for validating UTF-8 <-> UTF-16 transcoding (UTF-16LE;
+UTF-16BE through a byte swap of each unit).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg load this module; the library's code path never does.

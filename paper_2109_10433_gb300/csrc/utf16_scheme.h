@@ -79,6 +79,43 @@ GPUTF_HD uint32_t gputf_u16_counts(uint32_t c3, uint32_t hi, uint32_t lo, uint32
     return (N >> 7) + (A >> 7) + (B >> 6);
 }
 
+/*
+ * The UTF-8 bytes of one unit u that writes l bytes (its count above),
+ * followed by the unit `next`: the lead byte and the last three bytes, b1
+ * the last, b2 the one before, b3 the one before that.  l = 4 (the high
+ * half of a pair, `next` its low half) encodes the code point
+ *   c = ((u - 0xD800) << 10) + (next - 0xDC00) + 0x10000     (Section 3),
+ * l = 1, 2, 3 encode u itself: the lead carries the prefix 0 / 110 / 1110 /
+ * 11110 and the top bits, each continuation byte the prefix 10 and one
+ * 6-bit group (Section 5, Table 2).  Only the low byte of *lead counts; bytes
+ * beyond a unit's length carry no meaning (a lone surrogate's 2 bytes
+ * neither).  Two forms of the same bytes, for the kernel's two store orders:
+ * front to back (lead prefix by a shift of the four prefixes) and back to
+ * front (lead prefix by a byte permute; b3 always from c, whose bits 12-17
+ * are the third byte of a pair's encoding).
+ */
+GPUTF_HD void gputf_u16_utf8_bytes(uint32_t u, uint32_t next, uint32_t l, uint32_t *lead, uint32_t *b1,
+                                   uint32_t *b2, uint32_t *b3)
+{
+    const uint32_t c = (u << 10) + next - 0x35FDC00u;
+    const uint32_t y = l == 4 ? c : u;
+    *lead = gputf_fshr(y, 0u, 6 * l - 6) | gputf_fshr(0xF0E0C000u, 0u, 8 * l - 8);
+    *b1 = (y & 0x3F) | 0x80;
+    *b2 = ((y >> 6) & 0x3F) | 0x80;
+    *b3 = ((y >> 12) & 0x3F) | 0x80;
+}
+
+GPUTF_HD void gputf_u16_utf8_bytes_back(uint32_t u, uint32_t next, uint32_t l, uint32_t *lead, uint32_t *b1,
+                                        uint32_t *b2, uint32_t *b3)
+{
+    const uint32_t c = (u << 10) + next - 0x35FDC00u;
+    const uint32_t y = l == 4 ? c : u;
+    *lead = gputf_fshr(y, 0u, 6 * l - 6) | gputf_bperm(0xE0C00000u, 0xF0u, l);
+    *b1 = (y & 0x3F) | 0x80;
+    *b2 = ((y >> 6) & 0x3F) | 0x80;
+    *b3 = ((c >> 12) & 0x3F) | 0x80;
+}
+
 /* The pairing check across the end of a run: the last unit's "is high" (bit
  * 31 of hprev after the last group) against "the unit after is low". */
 GPUTF_HD uint32_t gputf_u16_end_mismatch(uint32_t hprev, uint32_t nu)

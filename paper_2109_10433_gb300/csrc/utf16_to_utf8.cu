@@ -118,11 +118,9 @@ __device__ __forceinline__ uint32_t byte_mask4(uint32_t x)
  */
 __device__ __forceinline__ void put_utf8(uint32_t sa, uint32_t u, uint32_t next, uint32_t l)
 {
-    const uint32_t c = (u << 10) + next - 0x35FDC00u;
-    const uint32_t y = l == 4 ? c : u;
     const uint32_t se = sa + l;                        /* sa: shared address of the lead byte; se: one past the last */
-    const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __funnelshift_r(0xF0E0C000u, 0u, 8 * l - 8);
-    const uint32_t b1 = (y & 0x3F) | 0x80, b2 = ((y >> 6) & 0x3F) | 0x80, b3 = ((y >> 12) & 0x3F) | 0x80;
+    uint32_t lead, b1, b2, b3;
+    gputf_u16_utf8_bytes(u, next, l, &lead, &b1, &b2, &b3);
     /* predicated stores: lead at o, continuation bytes at end-1, end-2, end-3
      * as far as the unit's length goes */
     asm volatile("{\n\t.reg .pred p1, p2, p3, p4;\n\t"
@@ -149,12 +147,9 @@ __device__ __forceinline__ void put_utf8(uint32_t sa, uint32_t u, uint32_t next,
  */
 __device__ __forceinline__ uint32_t put_utf8_back(uint32_t e, uint32_t u, uint32_t next, uint32_t l)
 {
-    const uint32_t c = (u << 10) + next - 0x35FDC00u;
-    const uint32_t y = l == 4 ? c : u;
     const uint32_t s = e - l;
-    /* lead prefix by length: bytes 0x00, 0xC0, 0xE0 of the first word, 0xF0 of the second */
-    const uint32_t lead = __funnelshift_r(y, 0u, 6 * l - 6) | __byte_perm(0xE0C00000u, 0xF0u, l);
-    const uint32_t b1 = (y & 0x3F) | 0x80, b2 = ((y >> 6) & 0x3F) | 0x80, b3 = ((c >> 12) & 0x3F) | 0x80;
+    uint32_t lead, b1, b2, b3;
+    gputf_u16_utf8_bytes_back(u, next, l, &lead, &b1, &b2, &b3);
     asm volatile("{\n\t.reg .pred p;\n\t"
                  "setp.ne.u32 p, %4, 0;\n\t"
                  "st.shared.u8 [%0+-3], %3;\n\t"

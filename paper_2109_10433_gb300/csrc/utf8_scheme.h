@@ -85,6 +85,7 @@ GPUTF_HD uint32_t gputf_fshr(uint32_t lo, uint32_t hi, uint32_t s)
 #if defined(__CUDA_ARCH__)
     return __funnelshift_r(lo, hi, s);
 #else
+    s &= 31;   /* the shift count taken modulo 32, as the device instruction takes it */
     return s ? (lo >> s) | (hi << (32 - s)) : lo;
 #endif
 }

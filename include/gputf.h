@@ -169,11 +169,22 @@ gputf_status gputf_utf8_length_from_utf16be(const uint16_t *in, size_t n_units, 
 
 /* Host-buffer forms of the two transcoders, for callers whose text lives in
  * host memory: copies `h_in` to the device buffer `d_in`, transcodes into
- * `d_out`, copies the result struct to `h_res` and the `written` output units
- * back to `h_out`.  Synchronous (returns after the copies are done).  The
- * device buffers are the caller's (`d_in` holds the input, `d_out` out_cap
- * units, `d_res` one gputf_result); pinned host memory makes the copies
- * fastest. */
+ * `d_out`, and copies the `written` output units back to `h_out`.  The
+ * result goes to `h_res` and to `d_res`.  The calls are synchronous: they
+ * return after the copies are done.  The device buffers are the caller's:
+ * `d_in` holds the input, `d_out` out_cap units, `d_res` one gputf_result.
+ * Pinned host memory makes the copies fastest.
+ *
+ * Inputs above 32 MiB are cut into chunks of about 32 MiB at the points
+ * gputf_utf8_chunk_end / gputf_utf16_chunk_end give.  All host -> device
+ * copies are issued at once.  Each chunk is transcoded on `stream` as soon as
+ * its input has arrived, at the output written so far, with the capacity
+ * left.  Its output is copied back while the next chunk is transcoded, so
+ * the copies in both directions and the kernels overlap.  The first chunk
+ * that reports an error or a full output ends the call.  `h_out`, `d_out` and
+ * the result are those of the single call on the whole input.  Each call
+ * creates two streams and some events and destroys them before it returns;
+ * it allocates no memory.  It must not run inside a stream capture. */
 gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
                                       size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
@@ -182,6 +193,35 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
                                       size_t out_cap, uint16_t *d_in, uint8_t *d_out, void *ws,
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream);
+
+/* The same with the chunk size chosen by the caller, in input code units.
+ * It is raised to 64, and to n / 63 when the input would need more than 64
+ * chunks.  The default forms above pass 32 MiB of input. */
+gputf_status gputf_utf8_to_utf16_host_chunked(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
+                                              size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
+                                              size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                              cudaStream_t stream, size_t chunk_bytes);
+gputf_status gputf_utf16_to_utf8_host_chunked(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
+                                              size_t out_cap, uint16_t *d_in, uint8_t *d_out, void *ws,
+                                              size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                              cudaStream_t stream, size_t chunk_units);
+
+/* Chunk boundaries for splitting one input into pieces transcoded by
+ * separate calls.  Each function returns a position p <= at, or n when
+ * at >= n.  The single call on in[0, n) gives the same result as the call
+ * on in[0, p) followed, when that one succeeds, by the call on in[p, n):
+ * the same output, written counts that add up, and the first error at the
+ * same position, shifted by p when it lies in the second piece.
+ *   UTF-8  : the last of in[at], in[at-1], in[at-2], in[at-3] that is not a
+ *            continuation byte (10xxxxxx), else `at`.  A character starts
+ *            there (Section 3, rule 3), or in[at] is a stray continuation
+ *            byte that no character can include (at most three follow a
+ *            lead).
+ *   UTF-16 : at - 1 when in[at - 1] is a high surrogate (Section 3: it pairs
+ *            with the unit after it, or is an error either way), else `at`.
+ * Host code only: `in` is host memory, read at most 4 units before `at`. */
+size_t gputf_utf8_chunk_end(const uint8_t *in, size_t n, size_t at);
+size_t gputf_utf16_chunk_end(const uint16_t *in, size_t n, size_t at);
 
 /* One direction of a batch: `count` strings stored back to back.
  *   in, in_offsets : device; string s is in[in_offsets[s] .. in_offsets[s+1])

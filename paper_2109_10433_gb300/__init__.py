@@ -58,6 +58,10 @@ SIGNATURES = {
     "gputf_utf8_length_from_utf16be": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_utf8_to_utf16_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
     "gputf_utf16_to_utf8_host": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P], _I),
+    "gputf_utf8_to_utf16_host_chunked": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P, _S], _I),
+    "gputf_utf16_to_utf8_host_chunked": ([_P, _S, _P, _S, _P, _P, _P, _S, _P, _P, _P, _S], _I),
+    "gputf_utf8_chunk_end": ([_P, _S, _S], _S),
+    "gputf_utf16_chunk_end": ([_P, _S, _S], _S),
     "gputf_utf16_to_utf8_static": ([_P, _S, _P, _S, _P, _P], _I),
     "gputf_batch_workspace_bytes": ([ctypes.c_uint64] * 4, _S),
     "gputf_batch_config_count": ([], _I),
@@ -274,23 +278,28 @@ def utf8_length_from_utf16(inp, ws: Workspace | None = None, out=None, stream=No
     return int(out.item()) if sync else out
 
 
-def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None) -> Result:
+def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None, chunk=None) -> Result:
     """Host-buffer form: h_in / h_out are CPU tensors (pinned for speed),
-    d_in / d_out / d_res device tensors of matching sizes."""
+    d_in / d_out / d_res device tensors of matching sizes.  `chunk` (input
+    bytes) overrides the size of the pieces whose copies and transcoding
+    overlap."""
     r = _CResult()
     n = h_in.numel() * h_in.element_size()
     cap = h_out.numel() * h_out.element_size() // 2
-    _check(lib().gputf_utf8_to_utf16_host(_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out),
-                                          ws.ptr, ws.nbytes, _ptr(d_res), ctypes.byref(r),
-                                          _stream(stream)), "gputf_utf8_to_utf16_host")
+    args = (_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out), ws.ptr, ws.nbytes, _ptr(d_res),
+            ctypes.byref(r), _stream(stream))
+    name = "gputf_utf8_to_utf16_host" if chunk is None else "gputf_utf8_to_utf16_host_chunked"
+    _check(getattr(lib(), name)(*args) if chunk is None else getattr(lib(), name)(*args, int(chunk)), name)
     return Result(r.error, r.position, r.written)
 
 
-def utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None) -> Result:
+def utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None, chunk=None) -> Result:
+    """As utf8_to_utf16_host, UTF-16LE in (`chunk` in input units)."""
     r = _CResult()
     n = h_in.numel() * h_in.element_size() // 2
     cap = h_out.numel() * h_out.element_size()
-    _check(lib().gputf_utf16_to_utf8_host(_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out),
-                                          ws.ptr, ws.nbytes, _ptr(d_res), ctypes.byref(r),
-                                          _stream(stream)), "gputf_utf16_to_utf8_host")
+    args = (_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out), ws.ptr, ws.nbytes, _ptr(d_res),
+            ctypes.byref(r), _stream(stream))
+    name = "gputf_utf16_to_utf8_host" if chunk is None else "gputf_utf16_to_utf8_host_chunked"
+    _check(getattr(lib(), name)(*args) if chunk is None else getattr(lib(), name)(*args, int(chunk)), name)
     return Result(r.error, r.position, r.written)

@@ -255,26 +255,157 @@ gputf_status gputf_utf8_length_from_utf16be(const uint16_t *in, size_t n_units, 
     return utf8_length_from_utf16_call(in, n_units, ws, ws_bytes, len, true, stream);
 }
 
+size_t gputf_utf8_chunk_end(const uint8_t *in, size_t n, size_t at)
+{
+    if (in == nullptr || at >= n) return n;
+    for (size_t k = 0; k < 4 && k <= at; k++)
+        if ((in[at - k] & 0xC0) != 0x80) return at - k;
+    return at;
+}
+
+size_t gputf_utf16_chunk_end(const uint16_t *in, size_t n, size_t at)
+{
+    if (in == nullptr || at >= n) return n;
+    return (at > 0 && (in[at - 1] & 0xFC00) == 0xD800) ? at - 1 : at;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr size_t HOST_MAX_CHUNKS = 64;
+
+/* Streams and events of one host-form call, released on every return path. */
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, arrived[HOST_MAX_CHUNKS] = {};
+    size_t events = 0;
+    ~HostPipe()
+    {
+        if (in) cudaStreamSynchronize(in);
+        if (out) cudaStreamSynchronize(out);
+        for (size_t k = 0; k < events; k++) cudaEventDestroy(arrived[k]);
+        if (start) cudaEventDestroy(start);
+        if (in) cudaStreamDestroy(in);
+        if (out) cudaStreamDestroy(out);
+    }
+};
+
+/*
+ * The host forms.  The input is cut into chunks of about `chunk` units at
+ * points where the single call's results do not depend on what lies beyond
+ * (gputf_*_chunk_end); all host -> device copies go out at once on one
+ * stream; each chunk is transcoded on the caller's stream, as soon as its
+ * input has arrived, into d_out at the output written so far, with the
+ * capacity left; its `written` units go back to h_out on a third stream while
+ * the next chunk is transcoded.  The first chunk that reports an error or a
+ * full output ends the call, its position moved to the whole input's.  So
+ * h_out, d_out and the result are the single call's.
+ */
+template <typename TIn, typename TOut, typename Call, typename Cut>
+gputf_status host_form(const TIn *h_in, size_t n, TOut *h_out, size_t out_cap, TIn *d_in, TOut *d_out,
+                       void *ws, size_t ws_bytes, gputf_result *d_res, gputf_result *h_res, cudaStream_t stream,
+                       size_t chunk, Call call, Cut cut)
+{
+    if ((n > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr || d_res == nullptr ||
+        (out_cap > 0 && (h_out == nullptr || d_out == nullptr)))
+        return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (chunk < 64) chunk = 64;
+    if (n / chunk >= HOST_MAX_CHUNKS) chunk = n / (HOST_MAX_CHUNKS - 1);
+    HostPipe p;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(p.start, stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p.in, p.start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p.out, p.start, 0)) != cudaSuccess)
+        return cuda_status(e);
+
+    /* chunk k is [a[k], a[k + 1]) */
+    size_t a[HOST_MAX_CHUNKS + 1];
+    size_t chunks = 0;
+    a[0] = 0;
+    while (a[chunks] < n || chunks == 0) {
+        const size_t next = chunks + 1 == HOST_MAX_CHUNKS ? n : cut(h_in, n, a[chunks] + chunk);
+        a[++chunks] = next;
+        if (next >= n) break;
+    }
+    for (size_t k = 0; k < chunks; k++) {
+        if ((e = cudaEventCreateWithFlags(&p.arrived[k], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_status(e);
+        p.events = k + 1;
+        const size_t len = a[k + 1] - a[k];
+        if (len && (e = cudaMemcpyAsync(d_in + a[k], h_in + a[k], len * sizeof(TIn), cudaMemcpyHostToDevice,
+                                        p.in)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = cudaEventRecord(p.arrived[k], p.in)) != cudaSuccess) return cuda_status(e);
+    }
+
+    gputf_result total = {GPUTF_E_OK, 0, (uint64_t)n, 0};
+    uint64_t done = 0;   /* output units written by the chunks so far */
+    for (size_t k = 0; k < chunks; k++) {
+        if ((e = cudaStreamWaitEvent(stream, p.arrived[k], 0)) != cudaSuccess) return cuda_status(e);
+        const gputf_status st = call(d_in + a[k], a[k + 1] - a[k], d_out + done, out_cap - done, ws, ws_bytes,
+                                     d_res, stream);
+        if (st != GPUTF_STATUS_OK) return st;
+        gputf_result r;
+        if ((e = cudaMemcpyAsync(&r, d_res, sizeof r, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+            return cuda_status(e);
+        const uint64_t w = r.written < out_cap - done ? r.written : out_cap - done;
+        if (w && (e = cudaMemcpyAsync(h_out + done, d_out + done, w * sizeof(TOut), cudaMemcpyDeviceToHost,
+                                      p.out)) != cudaSuccess)
+            return cuda_status(e);
+        done += w;
+        if (r.error != GPUTF_E_OK) {
+            total.error = r.error;
+            total.position = r.error == GPUTF_E_TIMEOUT ? 0 : a[k] + r.position;
+            total.written = r.error == GPUTF_E_TIMEOUT ? 0 : done;
+            break;
+        }
+        total.written = done;
+    }
+    if ((e = cudaStreamSynchronize(p.out)) != cudaSuccess || (e = cudaStreamSynchronize(p.in)) != cudaSuccess)
+        return cuda_status(e);
+    *h_res = total;
+    /* the device result as the single call leaves it */
+    if ((e = cudaMemcpyAsync(d_res, h_res, sizeof total, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+constexpr size_t HOST_CHUNK_BYTES = (size_t)32 << 20;   /* input bytes per chunk of the host forms */
+
+}  // namespace
+
+extern "C" {
+
+gputf_status gputf_utf8_to_utf16_host_chunked(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
+                                              size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
+                                              size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                              cudaStream_t stream, size_t chunk_bytes)
+{
+    return host_form(h_in, n_bytes, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res, h_res, stream, chunk_bytes,
+                     gputf_utf8_to_utf16, gputf_utf8_chunk_end);
+}
+
+gputf_status gputf_utf16_to_utf8_host_chunked(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
+                                              size_t out_cap, uint16_t *d_in, uint8_t *d_out, void *ws,
+                                              size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
+                                              cudaStream_t stream, size_t chunk_units)
+{
+    return host_form(h_in, n_units, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res, h_res, stream, chunk_units,
+                     gputf_utf16_to_utf8, gputf_utf16_chunk_end);
+}
+
 gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
                                       size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream)
 {
-    if ((n_bytes > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr ||
-        (out_cap > 0 && h_out == nullptr))
-        return GPUTF_STATUS_INVALID_ARGUMENT;
-    cudaError_t e;
-    if (n_bytes && (e = cudaMemcpyAsync(d_in, h_in, n_bytes, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-        return cuda_status(e);
-    gputf_status st = gputf_utf8_to_utf16(d_in, n_bytes, d_out, out_cap, ws, ws_bytes, d_res, stream);
-    if (st != GPUTF_STATUS_OK) return st;
-    if ((e = cudaMemcpyAsync(h_res, d_res, sizeof(gputf_result), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-        return cuda_status(e);
-    uint64_t w = h_res->written < out_cap ? h_res->written : out_cap;
-    if (w && (e = cudaMemcpyAsync(h_out, d_out, w * 2, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        return cuda_status(e);
-    return cuda_status(cudaStreamSynchronize(stream));
+    return gputf_utf8_to_utf16_host_chunked(h_in, n_bytes, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res,
+                                            h_res, stream, HOST_CHUNK_BYTES);
 }
 
 gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
@@ -282,22 +413,8 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream)
 {
-    if ((n_units > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr ||
-        (out_cap > 0 && h_out == nullptr))
-        return GPUTF_STATUS_INVALID_ARGUMENT;
-    cudaError_t e;
-    if (n_units &&
-        (e = cudaMemcpyAsync(d_in, h_in, n_units * 2, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-        return cuda_status(e);
-    gputf_status st = gputf_utf16_to_utf8(d_in, n_units, d_out, out_cap, ws, ws_bytes, d_res, stream);
-    if (st != GPUTF_STATUS_OK) return st;
-    if ((e = cudaMemcpyAsync(h_res, d_res, sizeof(gputf_result), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-        return cuda_status(e);
-    uint64_t w = h_res->written < out_cap ? h_res->written : out_cap;
-    if (w && (e = cudaMemcpyAsync(h_out, d_out, w, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        return cuda_status(e);
-    return cuda_status(cudaStreamSynchronize(stream));
+    return gputf_utf16_to_utf8_host_chunked(h_in, n_units, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res,
+                                            h_res, stream, HOST_CHUNK_BYTES / 2);
 }
 
 size_t gputf_batch_workspace_bytes(uint64_t units8, uint64_t count8, uint64_t units16, uint64_t count16)

@@ -235,6 +235,47 @@ def test_host_buffer_forms(g, ws):
     assert np.array_equal(h_out.numpy()[:r.written], ref_out)
 
 
+def test_host_forms_in_chunks(g, ws):
+    """The host forms cut into many chunks: every result, the host output,
+    the device output and the device result equal the single call's, with
+    errors and capacity ends placed near the cuts."""
+    rng = np.random.default_rng(12)
+    d_res = torch.empty(3, dtype=torch.int64, device="cuda")
+    clean8 = W.utf8_text(13, 200_000, W.MIX_FOUR_BYTE_HEAVY)
+    clean16 = W.utf16_text(14, 150_000, W.MIX_CJK_EMOJI)
+    for chunk in (64, 1000, 4099, 50_000):
+        for variant in range(4):
+            a = clean8.copy()
+            if variant:   # a corrupted byte next to where a chunk ends
+                a[min(a.size - 1, int(rng.integers(1, 8)) * chunk + int(rng.integers(-3, 4)))] = 0xFF
+            for cap in (a.size, int(rng.integers(1, a.size))):
+                h_in = torch.from_numpy(a).pin_memory()
+                h_out = torch.full((cap,), GUARD * 257, dtype=torch.int16).pin_memory()
+                d_in = torch.empty(a.size, dtype=torch.uint8, device="cuda")
+                d_out = torch.empty(cap, dtype=torch.int16, device="cuda")
+                r = g.utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws, d_res, chunk=chunk)
+                ref, ref_out = oracle.utf8_to_utf16(a, cap=cap)
+                assert tuple(r) == tuple(ref), (chunk, variant, cap, r, ref)
+                assert tuple(g.read_result(d_res)) == tuple(ref)
+                assert np.array_equal(h_out.numpy().view(np.uint16)[:r.written], ref_out)
+                assert np.array_equal(d_out.cpu().numpy().view(np.uint16)[:r.written], ref_out)
+        for variant in range(4):
+            u = clean16.copy()
+            if variant:   # a lone surrogate next to where a chunk ends
+                u[min(u.size - 1, int(rng.integers(1, 8)) * chunk + int(rng.integers(-2, 3)))] = 0xD800 + variant
+            for cap in (3 * u.size, int(rng.integers(1, 3 * u.size))):
+                h_in = torch.from_numpy(u.view(np.int16)).pin_memory()
+                h_out = torch.full((cap,), GUARD, dtype=torch.uint8).pin_memory()
+                d_in = torch.empty(u.size, dtype=torch.int16, device="cuda")
+                d_out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+                r = g.utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws, d_res, chunk=chunk)
+                ref, ref_out = oracle.utf16_to_utf8(u, cap=cap)
+                assert tuple(r) == tuple(ref), (chunk, variant, cap, r, ref)
+                assert tuple(g.read_result(d_res)) == tuple(ref)
+                assert np.array_equal(h_out.numpy()[:r.written], ref_out)
+                assert np.array_equal(d_out.cpu().numpy()[:r.written], ref_out)
+
+
 # ---------------------------------------------------------------------------
 # The benchmark workloads at full size
 # ---------------------------------------------------------------------------

@@ -149,6 +149,42 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
 
 
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def _on_device(t, what: str, min_bytes: int = 0):
+    """Checks a tensor whose address goes to a kernel.  The kernels read and
+    write t.data_ptr() as device memory, contiguously, for as many bytes as
+    the call's sizes say; a CPU tensor, a strided view or a short result
+    buffer would hand them the wrong memory, so those are refused here,
+    before anything is enqueued."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: expected a CUDA tensor, got one on {getattr(t, 'device', type(t))}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    if _nbytes(t) < min_bytes:
+        raise ValueError(f"{what}: {_nbytes(t)} bytes, at least {min_bytes} needed")
+    return t
+
+
+def _on_host(t, what: str):
+    """Checks a host buffer of the host-buffer forms (read or written by
+    cudaMemcpyAsync at t.data_ptr(), contiguously)."""
+    if getattr(t, "is_cuda", True):
+        raise ValueError(f"{what}: expected a CPU tensor (pinned for speed)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    return t
+
+
+def _utf16_units(t, what: str) -> int:
+    nb = _nbytes(t)
+    if nb % 2:
+        raise ValueError(f"{what}: UTF-16 input of {nb} bytes (an odd count)")
+    return nb // 2
+
+
 class Workspace:
     """Device scratch for the calls: a header and one status word per input
     tile.  Owned by PyTorch's allocator; prepared once here."""
@@ -182,9 +218,12 @@ class Workspace:
                "gputf_workspace_init")
 
 
-def _res_tensor(res):
+def _res_tensor(res, device):
+    """The caller's result tensor (24 bytes on the device), or a new one."""
     torch = _torch()
-    return res if res is not None else torch.empty(3, dtype=torch.int64, device="cuda")
+    if res is not None:
+        return _on_device(res, "res", 24)
+    return torch.empty(3, dtype=torch.int64, device=device)
 
 
 def read_result(res) -> Result:
@@ -193,9 +232,9 @@ def read_result(res) -> Result:
     return Result(int(v[0]) & 0xFFFFFFFF, int(v[1]), int(v[2]))
 
 
-def _ws_for(ws, n):
+def _ws_for(ws, n, device):
     if ws is None:
-        ws = Workspace(max(int(n), 1))
+        ws = Workspace(max(int(n), 1), device=device)
     return ws
 
 
@@ -213,13 +252,14 @@ def utf8_to_utf16(inp, out=None, ws: Workspace | None = None, res=None, stream=N
     big_endian).  Returns (Result, out) when sync, else (res tensor, out);
     `out` defaults to n units (torch.int16 storage).  validate=False calls the
     non-validating form."""
+    _on_device(inp, "inp")
     torch = _torch()
-    n = inp.numel() * inp.element_size()
+    n = _nbytes(inp)
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=inp.device)
-    cap = out.numel() * out.element_size() // 2
+    cap = _nbytes(_on_device(out, "out")) // 2
     name = _utf16_name("gputf_utf8_to_utf16", validate, big_endian)
-    ws, res = _ws_for(ws, n), _res_tensor(res)
+    ws, res = _ws_for(ws, n, inp.device), _res_tensor(res, inp.device)
     _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
@@ -229,41 +269,44 @@ def utf16_to_utf8(inp, out=None, ws: Workspace | None = None, res=None, stream=N
     """UTF-16LE units (UTF-16BE when big_endian; CUDA tensor of 2-byte
     elements) -> UTF-8 bytes.  `out` defaults to 3 bytes per unit
     (torch.uint8).  validate=False calls the non-validating form."""
+    n = _utf16_units(_on_device(inp, "inp"), "inp")
     torch = _torch()
-    n = inp.numel() * inp.element_size() // 2
     if out is None:
         out = torch.empty(max(3 * n, 1), dtype=torch.uint8, device=inp.device)
-    cap = out.numel() * out.element_size()
+    cap = _nbytes(_on_device(out, "out"))
     name = _utf16_name("gputf_utf16_to_utf8", validate, big_endian)
-    ws, res = _ws_for(ws, n), _res_tensor(res)
+    ws, res = _ws_for(ws, n, inp.device), _res_tensor(res, inp.device)
     _check(getattr(lib(), name)(_ptr(inp), n, _ptr(out), cap, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return (read_result(res) if sync else res), out
 
 
 def validate_utf8(inp, ws: Workspace | None = None, res=None, stream=None, sync=True):
-    n = inp.numel() * inp.element_size()
-    ws, res = _ws_for(ws, n), _res_tensor(res)
+    n = _nbytes(_on_device(inp, "inp"))
+    ws, res = _ws_for(ws, n, inp.device), _res_tensor(res, inp.device)
     _check(lib().gputf_validate_utf8(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)),
            "gputf_validate_utf8")
     return read_result(res) if sync else res
 
 
 def validate_utf16(inp, ws: Workspace | None = None, res=None, stream=None, sync=True, big_endian: bool = False):
-    n = inp.numel() * inp.element_size() // 2
-    ws, res = _ws_for(ws, n), _res_tensor(res)
+    n = _utf16_units(_on_device(inp, "inp"), "inp")
+    ws, res = _ws_for(ws, n, inp.device), _res_tensor(res, inp.device)
     name = "gputf_validate_utf16be" if big_endian else "gputf_validate_utf16"
     _check(getattr(lib(), name)(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(res), _stream(stream)), name)
     return read_result(res) if sync else res
 
 
-def _len_tensor(out):
+def _len_tensor(out, device):
+    """The caller's length tensor (8 bytes on the device), or a new one."""
     torch = _torch()
-    return out if out is not None else torch.empty(1, dtype=torch.int64, device="cuda")
+    if out is not None:
+        return _on_device(out, "out", 8)
+    return torch.empty(1, dtype=torch.int64, device=device)
 
 
 def utf16_length_from_utf8(inp, ws: Workspace | None = None, out=None, stream=None, sync=True):
-    n = inp.numel() * inp.element_size()
-    ws, out = _ws_for(ws, n), _len_tensor(out)
+    n = _nbytes(_on_device(inp, "inp"))
+    ws, out = _ws_for(ws, n, inp.device), _len_tensor(out, inp.device)
     _check(lib().gputf_utf16_length_from_utf8(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out),
                                               _stream(stream)), "gputf_utf16_length_from_utf8")
     return int(out.item()) if sync else out
@@ -271,11 +314,21 @@ def utf16_length_from_utf8(inp, ws: Workspace | None = None, out=None, stream=No
 
 def utf8_length_from_utf16(inp, ws: Workspace | None = None, out=None, stream=None, sync=True,
                            big_endian: bool = False):
-    n = inp.numel() * inp.element_size() // 2
-    ws, out = _ws_for(ws, n), _len_tensor(out)
+    n = _utf16_units(_on_device(inp, "inp"), "inp")
+    ws, out = _ws_for(ws, n, inp.device), _len_tensor(out, inp.device)
     name = "gputf_utf8_length_from_utf16be" if big_endian else "gputf_utf8_length_from_utf16"
     _check(getattr(lib(), name)(_ptr(inp), n, ws.ptr, ws.nbytes, _ptr(out), _stream(stream)), name)
     return int(out.item()) if sync else out
+
+
+def _host_form_buffers(h_in, h_out, d_in, d_out, d_res):
+    """The host forms copy all of h_in into d_in and read up to all of h_out's
+    capacity from d_out, so the device buffers must be at least as large."""
+    _on_host(h_in, "h_in")
+    _on_host(h_out, "h_out")
+    _on_device(d_in, "d_in", _nbytes(h_in))
+    _on_device(d_out, "d_out", _nbytes(h_out))
+    _on_device(d_res, "d_res", 24)
 
 
 def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None, chunk=None) -> Result:
@@ -283,9 +336,10 @@ def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=No
     d_in / d_out / d_res device tensors of matching sizes.  `chunk` (input
     bytes) overrides the size of the pieces whose copies and transcoding
     overlap."""
+    _host_form_buffers(h_in, h_out, d_in, d_out, d_res)
     r = _CResult()
-    n = h_in.numel() * h_in.element_size()
-    cap = h_out.numel() * h_out.element_size() // 2
+    n = _nbytes(h_in)
+    cap = _nbytes(h_out) // 2
     args = (_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out), ws.ptr, ws.nbytes, _ptr(d_res),
             ctypes.byref(r), _stream(stream))
     name = "gputf_utf8_to_utf16_host" if chunk is None else "gputf_utf8_to_utf16_host_chunked"
@@ -295,9 +349,10 @@ def utf8_to_utf16_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=No
 
 def utf16_to_utf8_host(h_in, h_out, d_in, d_out, ws: Workspace, d_res, stream=None, chunk=None) -> Result:
     """As utf8_to_utf16_host, UTF-16LE in (`chunk` in input units)."""
+    _host_form_buffers(h_in, h_out, d_in, d_out, d_res)
     r = _CResult()
-    n = h_in.numel() * h_in.element_size() // 2
-    cap = h_out.numel() * h_out.element_size()
+    n = _utf16_units(h_in, "h_in")
+    cap = _nbytes(h_out)
     args = (_ptr(h_in), n, _ptr(h_out), cap, _ptr(d_in), _ptr(d_out), ws.ptr, ws.nbytes, _ptr(d_res),
             ctypes.byref(r), _stream(stream))
     name = "gputf_utf16_to_utf8_host" if chunk is None else "gputf_utf16_to_utf8_host_chunked"

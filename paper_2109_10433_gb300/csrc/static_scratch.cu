@@ -50,8 +50,9 @@ extern "C" gputf_status gputf_utf16_to_utf8_static(const uint16_t *in, size_t n_
                                                    cudaStream_t stream)
 {
     if ((uint64_t)n_units > GPUTF_STATIC_MAX_UNITS) return GPUTF_STATUS_INPUT_TOO_LARGE;
-    if ((n_units > 0 && in == nullptr) || res == nullptr || (out_cap > 0 && out == nullptr))
-        return GPUTF_STATUS_INVALID_ARGUMENT;
+    if ((n_units > 0 && in == nullptr) || res == nullptr || (out_cap > 0 && out == nullptr) ||
+        ((uintptr_t)in & 1) || ((uintptr_t)res & 7))
+        return GPUTF_STATUS_INVALID_ARGUMENT;   /* refused before the set-up below touches the GPU */
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)

@@ -145,6 +145,8 @@ def test_static_entry_point_argument_checks(L):
     assert f(P(NULL), 10, P(A), 30, P(A), P(0)) == INVALID
     assert f(P(A), 10, P(A), 30, P(NULL), P(0)) == INVALID
     assert f(P(A), 10, P(NULL), 30, P(A), P(0)) == INVALID
+    assert f(P(A + 1), 10, P(A), 30, P(A), P(0)) == INVALID           # UTF-16 input not 2-byte aligned
+    assert f(P(A), 10, P(A), 30, P(A + 4), P(0)) == INVALID           # result not 8-byte aligned
 
 
 def test_batch_argument_checks(g, L):

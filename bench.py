@@ -44,6 +44,7 @@ KERNEL_SOURCES = ["paper_2109_10433_gb300/csrc/utf16_to_utf8.cu",
                   "paper_2109_10433_gb300/csrc/utf16_scheme.h",
                   "paper_2109_10433_gb300/csrc/utf8_scheme.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "utf16_to_utf8_256MiB_traffic.json")
+L2_BYTES = 129 * 10 ** 6   # GB300's L2 cache
 
 
 def kernel_source_hash() -> str:
@@ -220,14 +221,34 @@ def cpu_oracle_baseline(data: np.ndarray, min_seconds: float):
     return gbs, runs, el
 
 
+def workload_config(data: np.ndarray, out_bytes: int, world: int, mib: int) -> dict:
+    """The `config` object of the bench line, the same for both arms."""
+    return {"workload": WORKLOAD if mib == 256 else WORKLOAD.replace("256MiB", f"{mib}MiB"),
+            "input_bytes": int(data.nbytes),
+            "output_bytes": int(out_bytes), "chars": count_chars(data),
+            "l2": (f"input ({mib} MiB) larger than L2, no flush" if data.nbytes > L2_BYTES
+                   else f"input ({mib} MiB) fits in L2, no flush: L2-resident timing"),
+            "parallelism": f"replicas{world}"}
+
+
+def count_chars(data: np.ndarray) -> int:
+    """Characters of UTF-16 text: every unit but the low half of a pair
+    (a low surrogate right after a high one)."""
+    top = data & np.uint16(0xFC00)
+    low = top == 0xDC00
+    low[1:] &= top[:-1] == 0xD800
+    low[:1] = False
+    return int(data.size - np.count_nonzero(low))
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    data = W.cjk_emoji_utf16_256mib()
+    data = W.cjk_emoji_utf16_256mib(seed=rank_seed(0), nbytes=args.mib << 20)
     # each step: the oracle over a bounded 32 MiB slice of the workload
-    k = (32 << 20) // 2
-    if 0xD800 <= int(data[k - 1]) <= 0xDBFF:   # do not split a surrogate pair
+    k = min((32 << 20) // 2, data.size)
+    if k < data.size and 0xD800 <= int(data[k - 1]) <= 0xDBFF:   # do not split a surrogate pair
         k -= 1
     sample = data[:k]
     import oracle
@@ -246,15 +267,16 @@ def run_reference(args):
             assert all(r.error == 0 for r in rs)
     total = sum(times)
     value = args.steps * sample.nbytes / total / 1e9
+    out_bytes = oracle.utf8_length_from_utf16(data)   # the transcoded length (the text is valid)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "input_bytes": int(data.nbytes), "l2": "input larger than L2"},
+        "config": workload_config(data, out_bytes, world, args.mib),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                         "sample": f"first 32 MiB of the 256 MiB workload per step, in {cores} pair-safe "
-                                   "chunks, one oracle call per chunk on its own thread"},
+                         "sample": f"first {sample.nbytes >> 20} MiB of the {args.mib} MiB workload per step, "
+                                   f"in {cores} pair-safe chunks, one oracle call per chunk on its own thread"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -361,7 +383,7 @@ def run_gpu(args):
     algo_bytes = data.nbytes + out_bytes
     achieved = algo_bytes / avg_launch_s / 1e9
     traffic = ncu_traffic()
-    chars = int(np.count_nonzero((data & 0xFC00) != 0xDC00))
+    chars = count_chars(data)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -379,11 +401,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.mib == 256 else WORKLOAD.replace("256MiB", f"{args.mib}MiB"),
-                   "input_bytes": int(data.nbytes),
-                   "output_bytes": int(out_bytes), "chars": chars,
-                   "l2": "input (256 MiB) larger than L2, no flush",
-                   "parallelism": f"replicas{world}"},
+        "config": workload_config(data, out_bytes, world, args.mib),
         "gchar_s": world * args.steps * chars / (region_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

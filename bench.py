@@ -382,7 +382,7 @@ def run_gpu(args):
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     algo_bytes = data.nbytes + out_bytes
     achieved = algo_bytes / avg_launch_s / 1e9
-    traffic = ncu_traffic()
+    traffic = ncu_traffic() if args.mib == 256 else None   # the capture is of the 256 MiB launch
     chars = count_chars(data)
 
     cpu = None

@@ -32,15 +32,22 @@ REPS6 = np.array([0x41, 0x80, 0x90, 0xA0, 0xBF, 0xC1, 0xC2, 0xE0, 0xED, 0xEF, 0x
                   0xF8], dtype=np.uint8)
 
 
+CSRC = os.path.join(ROOT, "paper_2109_10433_gb300", "csrc")
+
+
 @pytest.fixture(scope="module")
 def checker(tmp_path_factory):
-    out = tmp_path_factory.mktemp("scheme") / "scheme_check.so"
+    return build_checker(tmp_path_factory.mktemp("scheme"))
+
+
+def build_checker(out_dir, csrc=CSRC):
+    """Builds the checker against the kernel headers in `csrc`."""
+    out = os.path.join(str(out_dir), "scheme_check.so")
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                           "-I" + os.path.join(ROOT, "oracle"),
-                           "-I" + os.path.join(ROOT, "paper_2109_10433_gb300", "csrc"),
-                           "-o", str(out), os.path.join(ROOT, "tests", "native", "scheme_check.c"),
+                           "-I" + os.path.join(ROOT, "oracle"), "-I" + csrc,
+                           "-o", out, os.path.join(ROOT, "tests", "native", "scheme_check.c"),
                            "-lpthread"])
-    lib = ctypes.CDLL(str(out))
+    lib = ctypes.CDLL(out)
     lib.scheme_check.restype = ctypes.c_uint64
     lib.scheme_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]

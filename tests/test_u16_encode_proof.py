@@ -35,15 +35,22 @@ REPS = np.array([0x0000, 0x0041, 0x007F, 0x0080, 0x00FF, 0x0100, 0x07FF, 0x0800,
                  0xFFFF], dtype=np.uint16)
 
 
+CSRC = os.path.join(ROOT, "paper_2109_10433_gb300", "csrc")
+
+
 @pytest.fixture(scope="module")
 def checker(tmp_path_factory):
-    out = tmp_path_factory.mktemp("u16encode") / "u16_encode_check.so"
+    return build_checker(tmp_path_factory.mktemp("u16encode"))
+
+
+def build_checker(out_dir, csrc=CSRC):
+    """Builds the checker against the kernel headers in `csrc`."""
+    out = os.path.join(str(out_dir), "u16_encode_check.so")
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                           "-I" + os.path.join(ROOT, "oracle"),
-                           "-I" + os.path.join(ROOT, "paper_2109_10433_gb300", "csrc"),
-                           "-o", str(out), os.path.join(ROOT, "tests", "native", "u16_encode_check.c"),
+                           "-I" + os.path.join(ROOT, "oracle"), "-I" + csrc,
+                           "-o", out, os.path.join(ROOT, "tests", "native", "u16_encode_check.c"),
                            "-lpthread"])
-    lib = ctypes.CDLL(str(out))
+    lib = ctypes.CDLL(out)
     lib.u16_encode_check.restype = ctypes.c_uint64
     lib.u16_encode_check.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int)]

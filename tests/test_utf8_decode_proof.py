@@ -23,14 +23,21 @@ FILL = np.array([0x00000000, 0xFFFFFFFF, 0x80808080, 0xBFBFBFBF, 0x41414141, 0xC
                  0xF0F0F0F0, 0x7F80BFC0, 0x12345678, 0xDEADBEEF, 0xF4908080], dtype=np.uint32)
 
 
+CSRC = os.path.join(ROOT, "paper_2109_10433_gb300", "csrc")
+
+
 @pytest.fixture(scope="module")
 def lib(tmp_path_factory):
-    out = tmp_path_factory.mktemp("decode") / "decode_check.so"
+    return build_checker(tmp_path_factory.mktemp("decode"))
+
+
+def build_checker(out_dir, csrc=CSRC):
+    """Builds the checker against the kernel headers in `csrc`."""
+    out = os.path.join(str(out_dir), "decode_check.so")
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                           "-I" + os.path.join(ROOT, "oracle"),
-                           "-I" + os.path.join(ROOT, "paper_2109_10433_gb300", "csrc"),
-                           "-o", str(out), os.path.join(ROOT, "tests", "native", "decode_check.c")])
-    L = ctypes.CDLL(str(out))
+                           "-I" + os.path.join(ROOT, "oracle"), "-I" + csrc,
+                           "-o", out, os.path.join(ROOT, "tests", "native", "decode_check.c")])
+    L = ctypes.CDLL(out)
     for f in (L.decode_check_scalars, L.decode_check_counts):
         f.restype = ctypes.c_uint64
         f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]

@@ -156,3 +156,46 @@ def test_chunk_end_edges(L):
     s = np.array([0xD83D, 0xDE00, 0x41], dtype=np.uint16)           # a pair, then 'A'
     assert [cut16(L, s)(at) for at in range(4)] == [0, 0, 2, 3]
     del e
+
+
+def _cut_breaks_results(fn, texts, cap_of, cut_of):
+    """True when some cut that `cut_of(text)` gives changes the combined
+    result or output against the single call on the whole text."""
+    for a in texts:
+        whole_r, whole_o = fn(a, cap=cap_of(a))
+        cut = cut_of(a)
+        for at in range(a.size + 1):
+            p = cut(at)
+            r, o = combined(fn, a, cap_of(a), [0, p, a.size] if 0 < p < a.size else [0, a.size])
+            if r != tuple(whole_r) or not np.array_equal(o, whole_o):
+                return True
+    return False
+
+
+def test_wrong_cut_rules_are_caught(L):
+    """The checks above fail for cut rules that are slightly wrong: a UTF-8
+    rule that looks back only three bytes (so a cut can fall after the third
+    byte of a four-byte character) and a UTF-16 rule that ignores surrogates
+    (so a cut can split a pair)."""
+    rng = np.random.default_rng(64)
+    t8 = [soup8(rng, int(rng.integers(10, 90))) for _ in range(40)]
+    t16 = [soup16(rng, int(rng.integers(10, 60))) for _ in range(40)]
+
+    def short8(a):
+        def cut(at):
+            if at >= a.size:
+                return a.size
+            for k in range(3):   # one byte short of the four a character can span
+                if k <= at and (int(a[at - k]) & 0xC0) != 0x80:
+                    return at - k
+            return at
+        return cut
+
+    def blind16(a):
+        return lambda at: min(at, a.size)
+
+    assert _cut_breaks_results(oracle.utf8_to_utf16, t8, lambda a: a.size, short8)
+    assert _cut_breaks_results(oracle.utf16_to_utf8, t16, lambda a: 3 * a.size, blind16)
+    # the library's rules on the same texts
+    assert not _cut_breaks_results(oracle.utf8_to_utf16, t8, lambda a: a.size, lambda a: cut8(L, a))
+    assert not _cut_breaks_results(oracle.utf16_to_utf8, t16, lambda a: 3 * a.size, lambda a: cut16(L, a))

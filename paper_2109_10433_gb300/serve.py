@@ -11,6 +11,8 @@ The loop (step):
   - completes every slot whose last launch has finished (a CUDA event),
     handing each of its requests its result and the arena view of its
     output, stamped with the completion time;
+  - drops, unrun, the waiting requests whose deadline (optional, host clock)
+    has passed; a waiting request can also be withdrawn with cancel();
   - fills every free slot with waiting requests in arrival order while they
     fit: a request takes its input bytes plus its output capacity from the
     slot's arena (admission by memory budget), and the first request that
@@ -61,6 +63,7 @@ class Request:
     done: float | None = None
     output: object | None = None  # kept output (a device tensor) when the server keeps outputs
     batch: int = -1              # index of the launch that served it
+    deadline: float | None = None  # host clock after which a request still waiting is dropped unrun
 
     @property
     def unit_bytes(self) -> int:
@@ -175,6 +178,9 @@ class Server:
         self.device_bytes = sum(s.device_bytes() for s in self.slots)
         self.waiting: list[Request] = []
         self.completed: list[Request] = []
+        self.cancelled: list[Request] = []   # withdrawn by cancel() while waiting
+        self.expired: list[Request] = []     # still waiting at their deadline, never run
+        self._deadlines = 0                  # waiting requests that carry a deadline
         self.batches = 0
         self.launches = 0           # library kernels enqueued
 
@@ -189,6 +195,32 @@ class Server:
         if self.footprint(r) + 4 * _ALIGN > self.slots[0].arena_bytes:
             raise ValueError(f"request {r.rid} ({r.in_bytes} bytes) does not fit a batch slot")
         self.waiting.append(r)
+        if r.deadline is not None:
+            self._deadlines += 1
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraws the waiting request `rid` (True), or does nothing (False)
+        when it is not waiting: a request already in a slot runs to the end."""
+        for k, r in enumerate(self.waiting):
+            if r.rid == rid:
+                del self.waiting[k]
+                if r.deadline is not None:
+                    self._deadlines -= 1
+                self.cancelled.append(r)
+                return True
+        return False
+
+    def _expire(self, now: float):
+        """Drops, unrun, the waiting requests whose deadline has passed."""
+        keep = []
+        for r in self.waiting:
+            if r.deadline is not None and now > r.deadline:
+                r.done = now
+                self.expired.append(r)
+                self._deadlines -= 1
+            else:
+                keep.append(r)
+        self.waiting = keep
 
     def _fill(self, slot: _Slot):
         taken = 0
@@ -201,6 +233,7 @@ class Server:
             slot.used += f
             taken += 1
         if taken:
+            self._deadlines -= sum(1 for r in self.waiting[:taken] if r.deadline is not None)
             del self.waiting[:taken]
 
     # ---- launch ---------------------------------------------------------
@@ -258,6 +291,8 @@ class Server:
         for slot in self.slots:
             if slot.in_flight and slot.event.query():
                 self._complete(slot, time.perf_counter())
+        if self._deadlines:
+            self._expire(time.perf_counter())
         for slot in self.slots:
             if not slot.in_flight and self.waiting:
                 self._fill(slot)

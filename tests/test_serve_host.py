@@ -10,7 +10,10 @@ its launch by a recorder, so the test sees what the loop itself decides:
   - a slot is launched once per fill and not refilled while in flight;
   - on completion every request of the slot gets the result row its
     placement names, and the slot is free again;
-  - requests that arrive while a slot is in flight go to another free slot.
+  - requests that arrive while a slot is in flight go to another free slot;
+  - a waiting request can be withdrawn, one in a slot cannot; a request
+    still waiting at its deadline is dropped unrun, and requests without a
+    deadline never are.
 """
 from types import SimpleNamespace
 
@@ -48,7 +51,8 @@ def fake_server(slots, max_requests=8):
     srv = object.__new__(S.Server)
     srv.slots = slots
     srv.max_requests = max_requests
-    srv.waiting, srv.completed = [], []
+    srv.waiting, srv.completed, srv.cancelled, srv.expired = [], [], [], []
+    srv._deadlines = 0
     srv.batches = 0
     srv.launched = []
 
@@ -143,3 +147,53 @@ def test_result_error_word_keeps_the_low_32_bits():
     slot.event.done = True
     srv.step()
     assert tuple(srv.completed[0].result) == (6, 4, 2)
+
+
+def test_cancel_withdraws_only_waiting_requests():
+    slot = fake_slot(0, 1 << 16, max_requests=2)
+    srv = fake_server([slot], max_requests=2)
+    for i in range(4):
+        srv.submit(req(i, 10))
+    srv.step()                                   # 0 and 1 go out, 2 and 3 wait
+    assert srv.cancel(0) is False                # in flight: runs to the end
+    assert srv.cancel(3) is True and srv.cancel(3) is False
+    assert [r.rid for r in srv.cancelled] == [3] and [r.rid for r in srv.waiting] == [2]
+    slot.event.done = True
+    srv.step()                                   # 0 and 1 complete, 2 goes out
+    slot.event.done = False
+    assert srv.launched[-1] == (0, [2])
+    slot.event.done = True
+    assert srv.step() is False
+    assert sorted(r.rid for r in srv.completed) == [0, 1, 2]
+
+
+def test_deadlines_drop_requests_still_waiting():
+    slot = fake_slot(0, 1 << 16, max_requests=1)
+    srv = fake_server([slot], max_requests=1)
+    now = S.time.perf_counter()
+    r0 = req(0, 10)
+    r0.deadline = now - 1.0                      # already past when the loop first runs
+    srv.submit(r0)
+    r1, r2, r3 = req(1, 10), req(2, 10), req(3, 10)
+    r1.deadline = now - 1.0                      # past: dropped while waiting
+    r2.deadline = now + 3600.0                   # far ahead: runs
+    for r in (r1, r2, r3):                       # r3 has no deadline
+        srv.submit(r)
+    assert srv._deadlines == 3
+    srv.step()
+    # expiry comes before filling: r0 and r1 are dropped unrun, r2 goes out
+    assert sorted(r.rid for r in srv.expired) == [0, 1]
+    assert all(r.result is None and r.done is not None for r in srv.expired)
+    assert srv.launched == [(0, [2])] and srv._deadlines == 0
+    slot.event.done = True
+    srv.step()
+    slot.event.done = False
+    assert srv.launched[-1] == (0, [3])
+    slot.event.done = True
+    assert srv.step() is False
+    assert sorted(r.rid for r in srv.completed) == [2, 3]
+
+
+def test_budget_too_small_for_the_slots_is_refused():
+    with pytest.raises(ValueError):
+        S.Server(budget_bytes=1 << 20, slots=4, max_requests=4096)

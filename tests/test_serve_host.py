@@ -197,3 +197,26 @@ def test_deadlines_drop_requests_still_waiting():
 def test_budget_too_small_for_the_slots_is_refused():
     with pytest.raises(ValueError):
         S.Server(budget_bytes=1 << 20, slots=4, max_requests=4096)
+
+
+def test_server_splits_the_budget_into_slots(monkeypatch):
+    """The constructor's arithmetic with stand-in slots: every slot's arena,
+    workspaces, metadata and result rows fit its share of the budget."""
+    made = []
+
+    class StandInSlot:
+        def __init__(self, index, arena_bytes, max_requests, ws_batch, ws_single, meta_bytes, device):
+            self.index, self.arena_bytes = index, arena_bytes
+            self.parts = (arena_bytes, ws_batch, ws_single, meta_bytes, 24 * max_requests)
+            made.append(self)
+
+        def device_bytes(self):
+            return sum(self.parts)
+
+    monkeypatch.setattr(S, "_Slot", StandInSlot)
+    srv = S.Server(budget_bytes=8 << 30, slots=4, max_requests=4096)
+    assert len(made) == 4 and all(s.arena_bytes % A == 0 for s in made)
+    assert all(s.device_bytes() <= (8 << 30) // 4 for s in made)
+    assert srv.device_bytes <= 8 << 30
+    assert made[0].arena_bytes > (8 << 30) // 4 * 0.9          # the arena takes most of the share
+    assert srv.waiting == [] and srv.expired == [] and srv.cancelled == [] and srv._deadlines == 0

@@ -45,6 +45,7 @@ KERNEL_SOURCES = ["paper_2109_10433_gb300/csrc/utf16_to_utf8.cu",
                   "paper_2109_10433_gb300/csrc/utf8_scheme.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "utf16_to_utf8_256MiB_traffic.json")
 L2_BYTES = 129 * 10 ** 6   # GB300's L2 cache
+BATCH_SEED, SERVE_SEED = 3, 4
 
 
 def kernel_source_hash() -> str:
@@ -228,7 +229,7 @@ def workload_config(data: np.ndarray, out_bytes: int, world: int, mib: int) -> d
             "output_bytes": int(out_bytes), "chars": count_chars(data),
             "l2": (f"input ({mib} MiB) larger than L2, no flush" if data.nbytes > L2_BYTES
                    else f"input ({mib} MiB) fits in L2, no flush: L2-resident timing"),
-            "parallelism": f"replicas{world}"}
+            "parallelism": f"replicas{world}", "seeds": [rank_seed(r) for r in range(world)]}
 
 
 def count_chars(data: np.ndarray) -> int:
@@ -434,7 +435,7 @@ def run_batch(args):
 
     g.build()
     torch.cuda.set_device(0)
-    bt = W.string_batch(3, args.strings)
+    bt = W.string_batch(BATCH_SEED, args.strings)
     s8 = [s for s, d in zip(bt.strings, bt.directions) if d == 0]
     s16 = [s for s, d in zip(bt.strings, bt.directions) if d == 1]
     b8 = B.DeviceBatch(s8, B.UTF8_TO_UTF16)
@@ -502,7 +503,7 @@ def run_batch(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "dtype": "u8/u16",
         "data": "synthetic",
         "config": {"workload": f"batch_{n_strings}_strings_lognormal_median1KiB_half_each_direction",
-                   "input_bytes": int(in_bytes), "tile_config": cfg, "graph": True},
+                   "input_bytes": int(in_bytes), "tile_config": cfg, "graph": True, "seed": BATCH_SEED},
         "input_gbs": in_bytes / (ms * 1e-3) / 1e9,
         "invalid_strings": bad,
         "per_string_launches": {"strings": len(calls), "seconds": per_s,
@@ -532,7 +533,7 @@ def run_serve(args):
     g.build()
     torch.cuda.set_device(0)
     t_gen = time.perf_counter()
-    w = W.serve_workload(4, args.requests)
+    w = W.serve_workload(SERVE_SEED, args.requests)
     gen_s = time.perf_counter() - t_gen
     pool = S.DevicePool(list(w.texts) + list(w.payloads))
     nt = len(w.texts)
@@ -614,7 +615,7 @@ def run_serve(args):
         "config": {"workload": f"serve_{w.units.size}_requests_loguniform_64B_16MiB_poisson",
                    "input_bytes": in_bytes, "budget_bytes": srv.budget_bytes, "device_bytes": srv.device_bytes,
                    "slots": len(srv.slots), "max_requests_per_slot": srv.max_requests, "big_units": srv.big_units,
-                   "validate_only_requests": int(w.validate_only.sum()), "generation_s": gen_s},
+                   "validate_only_requests": int(w.validate_only.sum()), "generation_s": gen_s, "seed": SERVE_SEED},
         "saturated": sat, "levels": levels,
         "p50_ms": levels[1]["p50_ms"], "p99_ms": levels[1]["p99_ms"],
         "invalid_requests": invalid, "results_identical_to_standalone": same,

@@ -645,7 +645,7 @@ def run_passes(args):
     s = torch.cuda.current_stream()
     sp = g._stream(s)
     u16 = W.cjk_emoji_utf16_256mib(nbytes=args.mib << 20)
-    u8 = W.utf8_text(2, 64 << 20, W.MIX_FOUR_BYTE_HEAVY)
+    u8 = W.utf8_text(2, args.u8_mib << 20, W.MIX_FOUR_BYTE_HEAVY)
     d16 = torch.from_numpy(u16.view(np.int16).copy()).cuda()
     d8 = torch.from_numpy(u8.copy()).cuda()
     n16, n8 = int(u16.size), int(u8.size)
@@ -665,7 +665,7 @@ def run_passes(args):
     len16 = g.utf16_length_from_utf8(d8, ws=ws)
     len16s = g.utf16_length_from_utf8(d8s, ws=ws)
     inputs = {"utf16": ("utf16 %d MiB cjk/emoji" % args.mib, 2 * n16),
-              "utf8": ("utf8 64 MiB four-byte-heavy", n8),
+              "utf8": ("utf8 %d MiB four-byte-heavy" % args.u8_mib, n8),
               "utf8_l2": ("utf8 1 MiB latin/cyrillic, L2-resident", n8s)}
     cases = [
         ("utf16_to_utf8", "utf16", lambda: L.gputf_utf16_to_utf8(g._ptr(d16), n16, g._ptr(out8), 3 * n16, ws.ptr,
@@ -811,6 +811,8 @@ def main():
     ap.add_argument("--mib", type=int, default=256,
                     help="input MiB of the UTF-16 workload (256 is the measured configuration; "
                          "smaller sizes are for profiler captures)")
+    ap.add_argument("--u8-mib", type=int, default=64,
+                    help="input MiB of the four-byte-heavy UTF-8 workload in --workload passes")
     ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve", "passes", "sweep"])
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--budget-gb", type=int, default=8)

@@ -626,18 +626,32 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
     uint64_t first_err = NONE;
     uint64_t tile = blockIdx.x;
     uint32_t w[WORDS];
-    if (tile < tiles) load_chunk16<WORDS>(base, tile * TILE + (uint64_t)tid * UPT, head, endx, w);
+    /* lanes 0 and 31 also need the unit before / after their warp's span
+     * (another warp's): loaded with the chunk, one tile ahead like the rest */
+    uint32_t side = 0;
+    auto side_unit = [&](uint64_t e0) -> uint32_t {
+        if (lane == 0) return unit_at(base, (long long)e0 - 1, head, endx);
+        if (lane == 31) return unit_at(base, (long long)(e0 + UPT), head, endx);
+        return 0u;
+    };
+    if (tile < tiles) {
+        load_chunk16<WORDS>(base, tile * TILE + (uint64_t)tid * UPT, head, endx, w);
+        side = side_unit(tile * TILE + (uint64_t)tid * UPT);
+    }
     while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * UPT;
         const uint64_t next = tile + gridDim.x;
-        uint32_t v[WORDS];
-        if (next < tiles) load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
+        uint32_t v[WORDS], v_side = 0;
+        if (next < tiles) {
+            load_chunk16<WORDS>(base, next * TILE + (uint64_t)tid * UPT, head, endx, v);
+            v_side = side_unit(next * TILE + (uint64_t)tid * UPT);
+        }
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = units_of<BE>(w[k]);
         uint32_t pu = __shfl_up_sync(FULL_MASK, w[WORDS - 1] >> 16, 1);
         uint32_t nu = __shfl_down_sync(FULL_MASK, w[0] & 0xFFFF, 1);
-        if (lane == 0) pu = unit_of<BE>(unit_at(base, (long long)e0 - 1, head, endx));
-        if (lane == 31) nu = unit_of<BE>(unit_at(base, (long long)(e0 + UPT), head, endx));
+        if (lane == 0) pu = unit_of<BE>(side);
+        if (lane == 31) nu = unit_of<BE>(side);
         /* units outside the input read as zero, which is no surrogate, so a
          * broken pair always has an input unit to blame */
         if (surrogate_mismatch<WORDS>(w, pu, nu) && first_err == NONE) {
@@ -655,6 +669,7 @@ validate_utf16_kernel(const uint16_t *__restrict__ in, uint64_t n, uint64_t tile
         }
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];
+        side = v_side;
         tile = next;
     }
     if (__syncthreads_or(first_err != NONE)) {

@@ -506,15 +506,24 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
     uint64_t tile = blockIdx.x;
     uint32_t w[WORDS];
     bool interior = false;
-    if (tile < tiles) interior = load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
+    /* lane 0 also needs the word before its chunk (another warp's): it is
+     * loaded with the chunk, one tile ahead like the rest */
+    uint32_t before = 0;
+    if (tile < tiles) {
+        interior = load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
+        if (lane == 0) before = word_at(base, (long long)(tile * TILE + (uint64_t)tid * BPT) - 4, head, endx);
+    }
     while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
         const uint64_t next = tile + gridDim.x;
-        uint32_t v[WORDS];
+        uint32_t v[WORDS], v_before = 0;
         bool v_interior = false;
-        if (next < tiles) v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
+        if (next < tiles) {
+            v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
+            if (lane == 0) v_before = word_at(base, (long long)(next * TILE + (uint64_t)tid * BPT) - 4, head, endx);
+        }
         uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
-        if (lane == 0) pw = word_at(base, (long long)e0 - 4, head, endx);
+        if (lane == 0) pw = before;
         uint32_t any = pw;
 #pragma unroll
         for (int k = 0; k < WORDS; k++) any |= w[k];
@@ -539,6 +548,7 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];
         interior = v_interior;
+        before = v_before;
         tile = next;
     }
     if (__syncthreads_or(first_err != NONE)) {
@@ -585,7 +595,7 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
         uint32_t v[WORDS];
         bool v_interior = false;
         if (next < tiles) v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
-        uint32_t c = 0;
+        uint32_t c = 0;   /* per-byte counts, at most 2 a word: 16 a byte */
 #pragma unroll
         for (int k = 0; k < WORDS; k++) {
             const uint32_t x = w[k];
@@ -596,9 +606,9 @@ utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64
                 lead &= rm;
                 f4 &= rm;
             }
-            c += __popc(lead) + __popc(f4);
+            c += (lead >> 7) + (f4 >> 7);
         }
-        acc += c;
+        acc += (c * 0x01010101u) >> 24;
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];
         interior = v_interior;

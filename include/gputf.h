@@ -98,8 +98,10 @@ typedef struct gputf_result {
 size_t gputf_workspace_bytes(size_t max_units);
 
 /* Prepares a workspace (device memory, `ws_bytes` long) for use; enqueued on
- * `stream`.  Needed once after allocation, and again after a call reported
- * GPUTF_TIMEOUT. */
+ * `stream`.  Needed once after allocation.  Every call leaves the workspace
+ * ready for the next one, including a call that reported GPUTF_TIMEOUT (its
+ * last thread block resets the header and moves the call epoch on); running
+ * this again is harmless. */
 gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Validating UTF-8 -> UTF-16LE (Sections 3-4).
@@ -399,13 +401,32 @@ gputf_status gputf_serve_launch(const gputf_slot *slot, const gputf_request *req
  *     GPUTF_STATUS_INPUT_TOO_LARGE; use gputf_utf16_to_utf8 for those.
  *   - The first call on each device sets the scratch up (it looks up the
  *     array's device address and enqueues its initialisation on `stream`);
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture: made on a stream that
+ *     is being captured, it returns GPUTF_STATUS_INVALID_ARGUMENT and does
+ *     nothing.  The set-up is remembered per device for the life of the
+ *     process, in the primary context: after cudaDeviceReset, or from
+ *     another context on the same device, this call is not valid.
+ *   - A call that reports GPUTF_TIMEOUT leaves the scratch ready for the
+ *     next call, as for a workspace (its last thread block resets it).
  *   - All calls on a device share the one array: calls that overlap on the
  *     GPU (on different streams without ordering) race and must be avoided.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     routine. */
 gputf_status gputf_utf16_to_utf8_static(const uint16_t *in, size_t n_units, uint8_t *out,
                                         size_t out_cap, gputf_result *res, cudaStream_t stream);
+
+/* Failure detection, for tests: runs one of the kernels' bounded waits until
+ * it gives up, as a call whose data never arrives would (the paper has no
+ * counterpart).  which = 0: the decoupled look-back of the output offsets
+ * (A3), polling the status word of a tile that never publishes; which = 1:
+ * the wait on a shared-memory barrier that a tile copy completes (A1), with
+ * no copy issued.  `polls` (1 .. 2^20) replaces the kernels' limit, which is
+ * about a second.  `ws` is a prepared workspace with room for at least one
+ * tile; `res` (device) receives GPUTF_TIMEOUT, position 0, written 0, and the
+ * workspace is left ready for the next call, as after any call that timed
+ * out.  Enqueued on `stream`; faults nothing, allocates nothing. */
+gputf_status gputf_test_wait_timeout(void *ws, size_t ws_bytes, int which, uint32_t polls, gputf_result *res,
+                                     cudaStream_t stream);
 
 /* Names of codes, for messages. */
 const char *gputf_error_name(int32_t error);

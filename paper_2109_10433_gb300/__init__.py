@@ -63,6 +63,7 @@ SIGNATURES = {
     "gputf_utf8_chunk_end": ([_P, _S, _S], _S),
     "gputf_utf16_chunk_end": ([_P, _S, _S], _S),
     "gputf_utf16_to_utf8_static": ([_P, _S, _P, _S, _P, _P], _I),
+    "gputf_test_wait_timeout": ([_P, _S, _I, ctypes.c_uint32, _P, _P], _I),
     "gputf_batch_workspace_bytes": ([ctypes.c_uint64] * 4, _S),
     "gputf_batch_config_count": ([], _I),
     "gputf_batch_transcode": ([_P, _P, _I, _P, _S, _P], _I),

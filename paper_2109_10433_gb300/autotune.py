@@ -21,10 +21,23 @@ CACHE_PATH = os.environ.get("GPUTF_AUTOTUNE_CACHE",
 _lock = threading.Lock()
 
 
+def driver_version() -> int:
+    """The installed CUDA driver's version (cuDriverGetVersion), 0 if the
+    driver library cannot be asked."""
+    import ctypes
+    try:
+        v = ctypes.c_int(0)
+        if ctypes.CDLL("libcuda.so.1").cuDriverGetVersion(ctypes.byref(v)) == 0:
+            return int(v.value)
+    except OSError:
+        pass
+    return 0
+
+
 def _device_key() -> str:
     import torch
     p = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return f"{p.name}|{p.multi_processor_count}|{torch.version.cuda}"
+    return f"{p.name}|{p.multi_processor_count}|driver={driver_version()}"
 
 
 def mix_key(b8: B.DeviceBatch | None, b16: B.DeviceBatch | None) -> str:

@@ -93,10 +93,12 @@ constexpr int SPIN_LIMIT = 1 << 21;
  * Exclusive prefix of tile `tile` by decoupled look-back.  Called by all 32
  * lanes of one warp after the tile's aggregate has been published.  Each lane
  * reads one predecessor; the window moves back 32 tiles at a time until it
- * meets a tile that published its inclusive prefix.
+ * meets a tile that published its inclusive prefix.  A word still
+ * unpublished after `limit` polls is taken as a prefix of 0 and a timeout is
+ * recorded in *flags.
  */
 __device__ __forceinline__ uint64_t look_back(unsigned long long *status, long long tile,
-                                              unsigned epoch, unsigned *flags)
+                                              unsigned epoch, unsigned *flags, int limit = SPIN_LIMIT)
 {
     const int lane = threadIdx.x & 31;
     uint64_t exclusive = 0;
@@ -114,7 +116,7 @@ __device__ __forceinline__ uint64_t look_back(unsigned long long *status, long l
                     value = w & VALUE_MASK;
                     break;
                 }
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > limit) {
                     atomicOr(flags, FLAG_TIMEOUT);
                     flag = ST_PREFIX;
                     value = 0;
@@ -350,9 +352,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
  * little in hardware); past it the caller records a timeout. */
 constexpr int MBAR_SPIN_LIMIT = 1 << 22;
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int limit = MBAR_SPIN_LIMIT)
 {
-    for (int i = 0; i < MBAR_SPIN_LIMIT; i++)
+    for (int i = 0; i < limit; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -64,7 +64,12 @@ extern "C" gputf_status gputf_utf16_to_utf8_static(const uint16_t *in, size_t n_
         if (!st.ready) {
             /* set-up, once per device, with that device current: the array's
              * device address (the host-side symbol is not one), then the
-             * scratch is put in its starting state on the caller's stream */
+             * scratch is put in its starting state on the caller's stream.
+             * On a stream being captured that state would only be recorded,
+             * not reached, so the set-up is refused there. */
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return GPUTF_STATUS_CUDA_ERROR;
+            if (cap != cudaStreamCaptureStatusNone) return GPUTF_STATUS_INVALID_ARGUMENT;
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
                 return GPUTF_STATUS_CUDA_ERROR;

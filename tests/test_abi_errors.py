@@ -149,6 +149,18 @@ def test_static_entry_point_argument_checks(L):
     assert f(P(A), 10, P(A), 30, P(A + 4), P(0)) == INVALID           # result not 8-byte aligned
 
 
+def test_wait_timeout_entry_argument_checks(L):
+    f = L.gputf_test_wait_timeout
+    assert f(P(NULL), 4096, 0, 100, P(A), P(0)) == INVALID
+    assert f(P(A + 8), 4096, 0, 100, P(A), P(0)) == INVALID           # workspace not 16-byte aligned
+    assert f(P(A), 256, 0, 100, P(A), P(0)) == INVALID                # no room for a tile's status word
+    assert f(P(A), 4096, 2, 100, P(A), P(0)) == INVALID               # no such wait
+    assert f(P(A), 4096, 1, 0, P(A), P(0)) == INVALID                 # no polls
+    assert f(P(A), 4096, 1, (1 << 20) + 1, P(A), P(0)) == INVALID     # above the limit
+    assert f(P(A), 4096, 0, 100, P(NULL), P(0)) == INVALID
+    assert f(P(A), 4096, 0, 100, P(A + 4), P(0)) == INVALID           # result not 8-byte aligned
+
+
 def test_batch_argument_checks(g, L):
     from paper_2109_10433_gb300.batch import CBatch
 

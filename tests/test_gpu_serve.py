@@ -104,6 +104,27 @@ def test_served_results_equal_standalone_and_oracle(g, work):
     assert n_invalid >= int(work.invalid.sum()) > 0
 
 
+def test_served_form_at_full_request_sizes(g):
+    """The served form's own sizes: requests log-uniform from 64 B to 16 MiB
+    of input (a tenth of them 4 MiB or more), an 8 GiB admission budget over
+    four slots, the benchmark's split between batched and in-place requests,
+    Poisson arrivals that keep several slots busy.  Every result and every
+    output byte equals the oracle's and the single call's."""
+    from paper_2109_10433_gb300 import serve as S
+    w = W.serve_workload(9, 240)
+    sizes = w.input_bytes()
+    assert int((sizes >= 4 * MiB).sum()) >= 10 and int(sizes.max()) > 12 * MiB and int(sizes.min()) < 256
+    pool, reqs = build_requests(w)
+    srv = S.Server(budget_bytes=8 << 30, slots=4, max_requests=4096, big_units=1 << 20, keep_outputs=True)
+    rng = np.random.default_rng(1)
+    times = np.cumsum(rng.exponential(1e-4, len(reqs)))
+    S.run_arrivals(srv, reqs, times)
+    assert len(srv.completed) == len(reqs)
+    assert srv.batches >= 4
+    n_invalid = check_all(g, w, pool, reqs)
+    assert n_invalid >= int(w.invalid.sum())
+
+
 def test_one_request_at_a_time_equals_mix(g, work):
     """The same requests served one per batch give the same results as in
     the mix (a request's result does not depend on its batch)."""

@@ -3,7 +3,7 @@ that allocates nothing and keeps its scratch in a fixed array inside the
 library (for callers that cannot allocate device memory while they run).
 
 Its results and output must equal those of gputf_utf16_to_utf8 (which takes a
-workspace from the caller), exactly, on two calls in a row: the second call
+workspace from the caller) and the oracle's, exactly, on two calls in a row: the second call
 reuses the array as the first left it.  The file is collected last so that a
 run stopping at the first failure has run every other test before it."""
 import ctypes
@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -43,6 +44,10 @@ def _compare(g, units):
     got = g.read_result(res)
     assert tuple(got) == tuple(ref)
     assert torch.equal(out_new[:got.written], out_ref[:ref.written])
+    # and against the oracle itself, result and bytes
+    o_res, o_out = oracle.utf16_to_utf8(units)
+    assert tuple(got) == tuple(o_res)
+    assert np.array_equal(out_new[:got.written].cpu().numpy(), o_out)
     return got
 
 

@@ -7,9 +7,17 @@ validated and transcoded to UTF-8 by one kernel launch.  The input is larger
 than L2, so no flush is needed between steps.
 
 Prints one JSON line: input GB/s (device-timed, inputs resident in HBM), the
-same metric end to end through the host-buffer C-ABI call (copies included),
-the roofline of the kernel against the measured HBM copy bandwidth, SM clocks
-sampled during the timed region, and the CPU oracle's throughput on a sample.
+same metric end to end through the host-buffer C-ABI call (copies included)
+beside the host link's own copy ceiling, the roofline of the kernel against
+the measured HBM copy bandwidth, SM clocks sampled during the timed region,
+and the CPU oracle's throughput on a sample.  On one GPU the line also holds,
+under "configs", the other workloads, each timed on its own with its own
+clock record: the 1 MiB UTF-8 buffer, the 64 MiB error-injected UTF-8 buffer
+(and its mix at 256 MiB), every validate / length pass at 256 MiB, the
+100,000-string batch against per-string launches, the served request stream
+with p50 / p99 latency, and the input-size sweep; results are checked against
+the oracle (whole buffers, or the stated samples).  --headline-only skips
+them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -20,6 +28,7 @@ the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -374,6 +383,8 @@ def run_gpu(args):
             e2e_times.append(el)
     e2e_total = slowest(max(sum(e2e_times), 1e-12), dev)
     e2e_val = replica_gbs(world, data.nbytes, len(e2e_times), e2e_total) if e2e_times else None
+    ceiling = e2e_ceiling(h_in, h_out[:out_bytes], inp, out[:out_bytes]) if rank == 0 else None
+    del h_in, h_out
 
     if rank != 0:
         torch.distributed.destroy_process_group()
@@ -409,18 +420,199 @@ def run_gpu(args):
                      "algorithmic_bytes": int(algo_bytes), "kernel": KERNEL,
                      "avg_launch_us": avg_launch_s * 1e6, "peak_source": peak_kind},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(data.nbytes),
-                "d2h_bytes_per_step": int(out_bytes + 24), "steps": len(e2e_times)},
+                "d2h_bytes_per_step": int(out_bytes + 24), "steps": len(e2e_times),
+                "copy_ceiling": ceiling,
+                "frac_of_copy_ceiling": (e2e_val / ceiling["input_gbs_ceiling"]) if (ceiling and e2e_val) else None},
         "gpu_launches": args.steps,
         "clocks": clock_info,
         "cpu_baseline": cpu,
     }
+    if world == 1 and not args.headline_only:
+        # the other configurations, each timed on its own with its own clock
+        # record (outside the headline's timed region)
+        del inp, out, ws, res
+        torch.cuda.empty_cache()
+        sections = {}
+        for name, fn in (("config1_utf8_1MiB", config1_section), ("config3_utf8_64MiB_errors", config3_section),
+                         ("passes_256MiB", passes_section), ("config4_batch", batch_section),
+                         ("config5_serve", serve_section), ("sweep", sweep_section)):
+            t0 = time.perf_counter()
+            sections[name] = fn(args)
+            sections[name]["section_s"] = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        line["configs"] = sections
+        sv = sections["config5_serve"]
+        line["serving_p99_ms"] = sv["p99_ms"]
+        line["serving_p50_ms"] = sv["p50_ms"]
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def event_times(fn, stream, reps, before=None):
+    """Device time (ms) of each of `reps` calls of fn, CUDA events on the
+    launching stream; `before` (not timed) runs ahead of each call."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        if before is not None:
+            before()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = fn()
+        e1.record(stream)
+        if st not in (None, 0):
+            raise RuntimeError(f"call status {st}")
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def device_uuid():
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return None
+
+
+def config1_section(args):
+    """Configuration 1: one 1 MiB UTF-8 buffer (90% U+0020-007E, 10%
+    U+0400-04FF, seed 0) to UTF-16LE with validation.  It fits in L2 and a
+    launch costs more than its bytes: reported in microseconds per call
+    (no flush, L2-resident), with the output checked against the oracle."""
+    import torch
+
+    import oracle
+    import paper_2109_10433_gb300 as g
+    data = W.latin_cyrillic_utf8_1mib()
+    n = int(data.size)
+    d = torch.from_numpy(data.copy()).cuda()
+    out = torch.empty(n, dtype=torch.int16, device="cuda")
+    ws = g.Workspace(n + 16)
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    L = g.lib()
+    fn = lambda: L.gputf_utf8_to_utf16(g._ptr(d), n, g._ptr(out), n, ws.ptr, ws.nbytes, g._ptr(res), g._stream(s))
+    event_times(fn, s, 5)
+    clocks = ClockSampler(device_uuid())
+    clocks.start()
+    ms = event_times(fn, s, 200)
+    clk = clocks.stop()
+    r = g.read_result(res)
+    ref, ref_out = oracle.utf8_to_utf16(data)
+    exact = tuple(r) == tuple(ref) and np.array_equal(out[:r.written].cpu().numpy().view(np.uint16), ref_out)
+    us = statistics.median(ms) * 1e3
+    peak, _ = measured_peak()
+    algo = n + 2 * int(r.written)
+    return {"workload": "utf8_to_utf16le_validating_1MiB_ascii90_cyrillic10", "seed": 0, "input_bytes": n,
+            "output_units": int(r.written), "median_us": us, "min_us": min(ms) * 1e3, "calls": len(ms),
+            "input_gbs": n / (us * 1e-6) / 1e9, "gchar_s": int(r.written) / (us * 1e-6) / 1e9,
+            "achieved_gbs": algo / (us * 1e-6) / 1e9, "frac": algo / (us * 1e-6) / 1e9 / peak,
+            "l2": "1 MiB fits in L2; no flush (L2-resident, launch-bound)", "identical_to_oracle": bool(exact),
+            "clocks": clk}
+
+
+def config3_section(args):
+    """Configuration 3: 64 MiB of four-byte-heavy UTF-8 (40% U+10000-10FFFF,
+    30% U+0800-FFFF without surrogates, 30% ASCII; seed 2) with error tokens
+    about once per MiB.  The full buffer's result (the first error: class,
+    offset, output count) and output are checked against the oracle; the
+    clean buffer (every token repaired) is timed with L2 flushed before each
+    call (a 512 MB write), and the same mix at 256 MiB (larger than L2, no
+    flush)."""
+    import torch
+
+    import oracle
+    import paper_2109_10433_gb300 as g
+    L = g.lib()
+    s = torch.cuda.current_stream()
+    sp = g._stream(s)
+    peak, _ = measured_peak()
+    et = W.four_byte_heavy_utf8_64mib()
+    n = int(et.data.size)
+    out = torch.empty(n, dtype=torch.int16, device="cuda")
+    ws = g.Workspace(4 * n + 16)
+    res = torch.zeros(3, dtype=torch.int64, device="cuda")
+    d = torch.from_numpy(et.data.copy()).cuda()
+    assert L.gputf_utf8_to_utf16(g._ptr(d), n, g._ptr(out), n, ws.ptr, ws.nbytes, g._ptr(res), sp) == 0
+    r = g.read_result(res)
+    ref, ref_out = oracle.utf8_to_utf16(et.data)
+    first_ok = (tuple(r) == tuple(ref) == (et.tokens[0][2], et.tokens[0][0], ref.written)
+                and np.array_equal(out[:r.written].cpu().numpy().view(np.uint16), ref_out))
+    clean = et.repaired_before(len(et.tokens))
+    d = torch.from_numpy(clean.copy()).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    fn = lambda: L.gputf_utf8_to_utf16(g._ptr(d), n, g._ptr(out), n, ws.ptr, ws.nbytes, g._ptr(res), sp)
+    event_times(fn, s, 3)
+    clocks = ClockSampler(device_uuid())
+    clocks.start()
+    ms = event_times(fn, s, 20, before=lambda: flush.fill_(1))
+    clk = clocks.stop()
+    rc = g.read_result(res)
+    us = statistics.median(ms) * 1e3
+    algo = n + 2 * int(rc.written)
+    row64 = {"input_bytes": n, "output_units": int(rc.written), "median_us": us, "min_us": min(ms) * 1e3,
+             "input_gbs": n / (us * 1e-6) / 1e9, "achieved_gbs": algo / (us * 1e-6) / 1e9,
+             "frac": algo / (us * 1e-6) / 1e9 / peak, "l2": "flushed before each call", "clean_ok": rc.error == 0,
+             "clocks": clk}
+    del d, flush
+    big = W.utf8_text(2, 256 << 20, W.MIX_FOUR_BYTE_HEAVY)
+    nb = int(big.size)
+    db = torch.from_numpy(big).cuda()
+    outb = torch.empty(nb, dtype=torch.int16, device="cuda")
+    fnb = lambda: L.gputf_utf8_to_utf16(g._ptr(db), nb, g._ptr(outb), nb, ws.ptr, ws.nbytes, g._ptr(res), sp)
+    event_times(fnb, s, 3)
+    clocks = ClockSampler(device_uuid())
+    clocks.start()
+    ms = event_times(fnb, s, 10)
+    clk = clocks.stop()
+    rb = g.read_result(res)
+    us = statistics.median(ms) * 1e3
+    algo = nb + 2 * int(rb.written)
+    row256 = {"input_bytes": nb, "output_units": int(rb.written), "median_us": us, "min_us": min(ms) * 1e3,
+              "input_gbs": nb / (us * 1e-6) / 1e9, "achieved_gbs": algo / (us * 1e-6) / 1e9,
+              "frac": algo / (us * 1e-6) / 1e9 / peak, "l2": "input larger than L2, no flush",
+              "clean_ok": rb.error == 0, "clocks": clk}
+    return {"workload": "utf8_to_utf16le_validating_64MiB_four_byte_heavy_errors_1_per_MiB", "seed": 2,
+            "error_tokens": len(et.tokens), "first_error": {"class": int(r.error), "position": int(r.position),
+                                                            "written": int(r.written)},
+            "first_error_identical_to_oracle": bool(first_ok), "clean_64MiB": row64, "clean_256MiB": row256,
+            "roofline_kernel": "utf8_to_utf16_kernel", "algorithmic_bytes": "n + 2 U (input bytes, output units)"}
+
+
+def e2e_ceiling(h_in, h_out, d_in, d_out, reps=5):
+    """The host link alone: the pinned input copied to the device while the
+    output is copied back, on two streams (as the host-buffer call overlaps
+    them), no kernel; and each direction alone."""
+    import torch
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    nin, nout = h_in.numel() * h_in.element_size(), d_out.numel() * d_out.element_size()
+
+    def one(h2d, d2h):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if h2d:
+            with torch.cuda.stream(a):
+                d_in.copy_(h_in, non_blocking=True)
+        if d2h:
+            with torch.cuda.stream(b):
+                h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    res = {}
+    for name, h2d, d2h in (("both", True, True), ("h2d", True, False), ("d2h", False, True)):
+        one(h2d, d2h)
+        res[name] = min(one(h2d, d2h) for _ in range(reps))
+    return {"h2d_bytes": nin, "d2h_bytes": nout, "both_s": res["both"], "h2d_s": res["h2d"], "d2h_s": res["d2h"],
+            "input_gbs_ceiling": nin / res["both"] / 1e9, "h2d_gbs": nin / res["h2d"] / 1e9,
+            "d2h_gbs": nout / res["d2h"] / 1e9}
+
+
+def batch_section(args):
     """Batched form: 100,000 strings (log-normal lengths, median 1 KiB,
     clipped 16 B - 64 KiB, per-string script, half in each direction, 1%
     invalid) in one graph-replayed launch with the autotuned tile shape,
@@ -497,6 +689,25 @@ def run_batch(args):
     same = all((int(got[j][0]) & 0xFFFFFFFF, int(got[j][1]), int(got[j][2])) == tuple(c[6])
                for j, c in enumerate(calls))
     bad = sum(1 for r in res8 + res16 if r.error != 0)
+    # the batched results and outputs of the same sample (and of every
+    # invalid string) against the oracle
+    import oracle
+    out8 = b8.out.cpu().numpy().view(np.uint16)
+    out16 = b16.out.cpu().numpy()
+    check = set(sample.tolist()) | {i for i in range(n_strings) if bt.invalid[i]}
+    oracle_ok = True
+    for i in sorted(check):
+        if bt.directions[i] == 0:
+            k = pos8[i]
+            ref, ref_out = oracle.utf8_to_utf16(bt.strings[i])
+            a = int(b8.out_offsets_host[k])
+            ok = tuple(res8[k]) == tuple(ref) and np.array_equal(out8[a:a + ref.written], ref_out)
+        else:
+            k = pos16[i]
+            ref, ref_out = oracle.utf16_to_utf8(bt.strings[i])
+            a = int(b16.out_offsets_host[k])
+            ok = tuple(res16[k]) == tuple(ref) and np.array_equal(out16[a:a + ref.written], ref_out)
+        oracle_ok = oracle_ok and ok
     line = {
         "metric": "batched transcoding strings/s (one graph-replayed launch) vs per-string launches",
         "value": n_strings / (ms * 1e-3), "unit": "strings/s", "n_gpus": 1, "steps": args.steps,
@@ -509,13 +720,19 @@ def run_batch(args):
         "per_string_launches": {"strings": len(calls), "seconds": per_s,
                                 "strings_per_s": len(calls) / per_s, "results_identical": same},
         "speedup_vs_per_string": (n_strings / (ms * 1e-3)) / (len(calls) / per_s),
+        "oracle_check": {"strings": len(check), "identical": bool(oracle_ok),
+                         "sample": "the per-string sample and every invalid string"},
         "gpu_launches": args.steps,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_batch(args):
+    print(json.dumps(batch_section(args)), flush=True)
     return 0
 
 
-def run_serve(args):
+def serve_section(args):
     """Served form: requests with Poisson arrivals, sizes log-uniform
     64 B - 16 MiB of input, scripts and directions as in the batched form,
     a fifth of them validate-only and 1% invalid, inputs resident on the
@@ -564,7 +781,15 @@ def run_serve(args):
         b0 = srv.batches
         clocks = ClockSampler(uuid)
         clocks.start()
-        t0 = S.run_arrivals(srv, reqs, times)
+        # the host loop runs in Python: its garbage collector is run before
+        # and held off during the run, so that a collection pause is not
+        # counted as serving latency
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = S.run_arrivals(srv, reqs, times)
+        finally:
+            gc.enable()
         clk = clocks.stop()
         t_end = max(r.done for r in reqs)
         lat = S.latency_ms(reqs)
@@ -608,6 +833,42 @@ def run_serve(args):
     same = all((int(got[j][0]) & 0xFFFFFFFF, int(got[j][1]), int(got[j][2])) == tuple(r.result)
                for j, r in enumerate(sat_reqs))
     invalid = sum(1 for r in sat_reqs if r.result.error != 0)
+    # served results and output bytes against the oracle: a seeded sample of
+    # the requests, every invalid one, and the largest ones
+    import oracle
+
+    def host_input(i):
+        src = int(w.source[i])
+        if src >= 0:
+            return w.texts[src][int(w.offset[i]):int(w.offset[i]) + int(w.units[i])]
+        return w.payloads[-1 - src]
+    pick = set(np.random.default_rng(1).choice(len(sat_reqs), size=min(args.oracle_sample, len(sat_reqs)),
+                                               replace=False).tolist())
+    pick |= {j for j, r in enumerate(sat_reqs) if r.result.error != 0}
+    pick |= set(np.argsort(w.units)[-10:].tolist())
+    # the picked requests served again, all at once, by a server of the same
+    # configuration that keeps their outputs: each result must be the timed
+    # run's, and result and bytes the oracle's
+    vsrv = S.Server(budget_bytes=args.budget_gb << 30, slots=args.slots, max_requests=args.max_requests,
+                    big_units=args.big_units, keep_outputs=True)
+    all_reqs = requests()
+    vreqs = [all_reqs[j] for j in sorted(pick)]
+    S.run_arrivals(vsrv, vreqs, np.zeros(len(vreqs)))
+    torch.cuda.synchronize()
+    oracle_ok = True
+    for r in vreqs:
+        if tuple(r.result) != tuple(sat_reqs[r.rid].result):
+            oracle_ok = False
+        h = host_input(r.rid)
+        if r.op == S.VALIDATE:
+            ref = (oracle.validate_utf8 if r.direction == 0 else oracle.validate_utf16)(h)
+            ok = tuple(r.result) == tuple(ref)
+        else:
+            ref, ref_out = (oracle.utf8_to_utf16 if r.direction == 0 else oracle.utf16_to_utf8)(h)
+            ub = 2 if r.direction == 0 else 1
+            got_b = r.output[:r.result.written * ub].cpu().numpy()
+            ok = tuple(r.result) == tuple(ref) and np.array_equal(got_b, ref_out.view(np.uint8))
+        oracle_ok = oracle_ok and ok
     line = {
         "metric": "served transcoding: sustained input GB/s with p50/p99 latency",
         "value": cap_gbs, "unit": "GB/s", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -619,20 +880,27 @@ def run_serve(args):
         "saturated": sat, "levels": levels,
         "p50_ms": levels[1]["p50_ms"], "p99_ms": levels[1]["p99_ms"],
         "invalid_requests": invalid, "results_identical_to_standalone": same,
+        "identical_to_oracle": bool(oracle_ok),
+        "oracle_check": {"requests": len(pick), "sample": f"{min(args.oracle_sample, len(sat_reqs))} seeded "
+                         "requests, every invalid one and the 10 largest, results and output bytes"},
         "gpu_launches": sat["gpu_launches"],
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serve(args):
+    print(json.dumps(serve_section(args)), flush=True)
     return 0
 
 
-def run_passes(args):
+def passes_section(args):
     """Every kernel of the path on its own: the two transcoders and the four
     validate / length passes, each timed per launch with CUDA events, with
     achieved algorithmic bytes per second against the measured HBM peak.
     UTF-16 input: the 256 MiB headline buffer (larger than L2).  UTF-8 input:
-    64 MiB of the 4-byte-heavy mix (40% U+10000-10FFFF, 30% U+0800-FFFF,
-    30% ASCII), valid; L2 is flushed (a 512 MB write) before every timed
-    launch; and the 1 MiB Latin/Cyrillic buffer (90% U+0020-007E, 10%
+    --u8-mib MiB (256 by default) of the 4-byte-heavy mix (40% U+10000-10FFFF,
+    30% U+0800-FFFF, 30% ASCII), valid; L2 is flushed (a 512 MB write) before
+    every timed launch; and the 1 MiB Latin/Cyrillic buffer (90% U+0020-007E, 10%
     U+0400-04FF), which stays in L2 (not flushed): a launch-bound case."""
     import torch
 
@@ -717,13 +985,16 @@ def run_passes(args):
                      "input_gbs": in_bytes / (us * 1e-6) / 1e9,
                      "achieved_gbs": gbs, "frac": gbs / peak})
     clk = clocks.stop()
-    print(json.dumps({"metric": "per-kernel algorithmic GB/s vs HBM roofline", "unit": "GB/s",
-                      "peak": peak, "peak_source": peak_kind, "steps": args.steps, "kernels": rows,
-                      "clocks": clk}), flush=True)
+    return {"metric": "per-kernel algorithmic GB/s vs HBM roofline", "unit": "GB/s",
+            "peak": peak, "peak_source": peak_kind, "steps": args.steps, "kernels": rows, "clocks": clk}
+
+
+def run_passes(args):
+    print(json.dumps(passes_section(args)), flush=True)
     return 0
 
 
-def run_sweep(args):
+def sweep_section(args):
     """Throughput against input size: single calls of both transcoders on
     sizes from 16 units to the whole buffer, and the batched call on many
     strings of one size (up to 64 Ki units), each timed over back-to-back
@@ -765,6 +1036,8 @@ def run_sweep(args):
         return e0.elapsed_time(e1) * 1e3 / reps
 
     rows = []
+    clocks = ClockSampler(device_uuid())
+    clocks.start()
     sizes = [16 << (2 * k) for k in range(12)] + [u16.size]
     for n in sizes:
         n16 = min(n, u16.size)
@@ -794,7 +1067,12 @@ def run_sweep(args):
             row.update({"batch_strings": count, "batch_us": usb, "batch_strings_per_s": count / (usb * 1e-6),
                         "batch_input_gbs": 2 * int(cuts[-1]) / usb / 1e3})
         rows.append(row)
-    print(json.dumps({"metric": "throughput vs input size (single calls and batched)", "sweep": rows}), flush=True)
+    clk = clocks.stop()
+    return {"metric": "throughput vs input size (single calls and batched)", "sweep": rows, "clocks": clk}
+
+
+def run_sweep(args):
+    print(json.dumps(sweep_section(args)), flush=True)
     return 0
 
 
@@ -811,7 +1089,7 @@ def main():
     ap.add_argument("--mib", type=int, default=256,
                     help="input MiB of the UTF-16 workload (256 is the measured configuration; "
                          "smaller sizes are for profiler captures)")
-    ap.add_argument("--u8-mib", type=int, default=64,
+    ap.add_argument("--u8-mib", type=int, default=256,
                     help="input MiB of the four-byte-heavy UTF-8 workload in --workload passes")
     ap.add_argument("--workload", default="utf16_256mib", choices=["utf16_256mib", "batch", "serve", "passes", "sweep"])
     ap.add_argument("--requests", type=int, default=20000)
@@ -821,6 +1099,9 @@ def main():
     ap.add_argument("--big-units", type=int, default=1 << 20)
     ap.add_argument("--strings", type=int, default=100000)
     ap.add_argument("--sample", type=int, default=2000)
+    ap.add_argument("--oracle-sample", type=int, default=400)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the 256 MiB UTF-16 -> UTF-8 configuration (profiler captures)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":
         return run_batch(args)

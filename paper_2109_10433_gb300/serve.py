@@ -64,6 +64,7 @@ class Request:
     output: object | None = None  # kept output (a device tensor) when the server keeps outputs
     batch: int = -1              # index of the launch that served it
     deadline: float | None = None  # host clock after which a request still waiting is dropped unrun
+    bypassed: int = 0            # times a later request was admitted while this one waited
 
     @property
     def unit_bytes(self) -> int:
@@ -222,19 +223,41 @@ class Server:
                 keep.append(r)
         self.waiting = keep
 
+    # A waiting request that does not fit what is left of a slot lets later
+    # requests that do fit go ahead of it, in at most MAX_BYPASS fills; after
+    # that it holds back every request behind it until a slot has room for
+    # it, so no request waits for ever.  Only LOOKAHEAD requests past the
+    # first one left behind are looked at per fill.
+    MAX_BYPASS = 8
+    LOOKAHEAD = 256
+
     def _fill(self, slot: _Slot):
-        taken = 0
         cap = slot.arena_bytes - 4 * _ALIGN   # the three group paddings of the layout
-        for r in self.waiting:
-            f = self.footprint(r)
-            if slot.used + f > cap or len(slot.requests) >= self.max_requests:
+        left: list[tuple[int, Request]] = []  # passed over: (position, request), in arrival order
+        last_taken = -1
+        k = 0
+        n = len(self.waiting)
+        while k < n and len(slot.requests) < self.max_requests:
+            if left and k - left[0][0] > self.LOOKAHEAD:
                 break
-            slot.requests.append(r)
-            slot.used += f
-            taken += 1
-        if taken:
-            self._deadlines -= sum(1 for r in self.waiting[:taken] if r.deadline is not None)
-            del self.waiting[:taken]
+            r = self.waiting[k]
+            f = self.footprint(r)
+            if slot.used + f <= cap:
+                slot.requests.append(r)
+                slot.used += f
+                last_taken = k
+                if r.deadline is not None:
+                    self._deadlines -= 1
+            else:
+                left.append((k, r))
+                if r.bypassed >= self.MAX_BYPASS:
+                    k += 1
+                    break
+            k += 1
+        for pos, r in left:
+            if pos < last_taken:   # a later request went ahead of it in this fill
+                r.bypassed += 1
+        self.waiting = [r for _, r in left] + self.waiting[k:]
 
     # ---- launch ---------------------------------------------------------
     def _launch(self, slot: _Slot):

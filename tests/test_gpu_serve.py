@@ -154,9 +154,10 @@ def test_one_request_at_a_time_equals_mix(g, work):
 
 
 def test_admission_order_budget_and_overlap(g, work):
-    """A small budget forces many batches: requests leave in arrival order,
-    no batch holds more than its arena, and the slots' launches overlap in
-    device time."""
+    """A small budget forces many batches: requests leave in arrival order
+    except where a later one that fits went ahead of one that did not (a
+    bounded number of times), no batch holds more than its arena, and the
+    slots' launches overlap in device time."""
     from paper_2109_10433_gb300 import serve as S
     pool, reqs = build_requests(work, extra_empty=False)
     # every request through the batched kernel, so that a batch's device time
@@ -167,8 +168,13 @@ def test_admission_order_budget_and_overlap(g, work):
         srv.submit(too_big)
     S.run_arrivals(srv, reqs, np.zeros(len(reqs)))
     torch.cuda.synchronize()
-    batches = [r.batch for r in sorted(reqs, key=lambda r: r.rid)]
-    assert batches == sorted(batches), "requests were served out of arrival order"
+    # a request is served after a later one only when that one went ahead
+    # of it while it did not fit, and that happens in a bounded number of fills
+    by_rid = sorted(reqs, key=lambda r: r.rid)
+    for i, r in enumerate(by_rid):
+        overtaken = any(q.batch < r.batch for q in by_rid[i + 1:])
+        assert not overtaken or r.bypassed >= 1, r.rid
+        assert r.bypassed <= S.Server.MAX_BYPASS, r.rid
     per_batch = {}
     for r in reqs:
         per_batch[r.batch] = per_batch.get(r.batch, 0) + srv.footprint(r)

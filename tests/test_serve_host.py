@@ -4,8 +4,9 @@ The server's slots are replaced by stand-ins (no stream, no device memory) and
 its launch by a recorder, so the test sees what the loop itself decides:
   - a free slot takes waiting requests in arrival order while their
     footprints (input bytes, output capacity, alignment slack) fit its arena,
-    and at most max_requests of them; the first request that does not fit
-    stops the filling, so no later request overtakes it;
+    and at most max_requests of them; a request that does not fit lets later
+    ones that do go ahead, in at most MAX_BYPASS fills, and then holds back
+    every request behind it until it is admitted;
   - a request larger than any slot is refused when submitted;
   - a slot is launched once per fill and not refilled while in flight;
   - on completion every request of the slot gets the result row its
@@ -85,11 +86,44 @@ def test_fill_in_arrival_order_within_the_arena():
     big = req(2, 3000)                          # 3000 + 6000 + 256 bytes
     srv.waiting = [req(0, 1000), req(1, 200), big, req(3, 10), req(4, 10)]
     srv._fill(slot)
-    # 3256 + 856 fit; the big one would pass the cap, so it and everything after it wait
-    assert [r.rid for r in slot.requests] == [0, 1]
-    assert [r.rid for r in srv.waiting] == [2, 3, 4]
-    assert slot.used == srv.footprint(slot.requests[0]) + srv.footprint(slot.requests[1])
+    # 3256 + 856 fit; the big one would pass the cap and waits, the two small
+    # ones after it go ahead of it
+    assert [r.rid for r in slot.requests] == [0, 1, 3, 4]
+    assert [r.rid for r in srv.waiting] == [2]
+    assert big.bypassed == 1
+    assert slot.used == sum(srv.footprint(r) for r in slot.requests)
     assert slot.used <= cap
+
+
+def test_a_request_left_behind_is_overtaken_a_bounded_number_of_times():
+    cap = 10 * 1024
+    srv = fake_server([fake_slot(0, cap + 4 * A)])
+    big = req(1, 3000)                          # 9256 bytes: fits only an empty slot
+    srv.waiting = [req(0, 300), big] + [req(2 + i, 300) for i in range(40)]
+    slot = fake_slot(0, cap + 4 * A)
+    srv._fill(slot)
+    assert slot.requests[0].rid == 0 and big in srv.waiting and big.bypassed == 1
+    slot = fake_slot(0, cap + 4 * A)            # the next free slot takes it first
+    srv._fill(slot)
+    assert slot.requests[0] is big
+    # once overtaken MAX_BYPASS times, nothing behind it goes ahead any more
+    srv = fake_server([fake_slot(0, cap + 4 * A)])
+    big = req(1, 3000)
+    big.bypassed = S.Server.MAX_BYPASS
+    srv.waiting = [req(0, 300), big] + [req(2 + i, 300) for i in range(10)]
+    slot = fake_slot(0, cap + 4 * A)
+    srv._fill(slot)
+    assert [r.rid for r in slot.requests] == [0]
+    assert [r.rid for r in srv.waiting] == list(range(1, 12))
+
+
+def test_lookahead_is_bounded():
+    cap = 10 * 1024
+    srv = fake_server([fake_slot(0, cap + 4 * A)], max_requests=10000)
+    srv.waiting = [req(0, 3000), req(1, 3000)] + [req(2 + i, 1) for i in range(1000)]
+    slot = fake_slot(0, cap + 4 * A, max_requests=10000)
+    srv._fill(slot)
+    assert len(slot.requests) <= S.Server.LOOKAHEAD + 2
 
 
 def test_fill_stops_at_max_requests():

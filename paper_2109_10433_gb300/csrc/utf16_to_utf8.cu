@@ -167,9 +167,12 @@ struct U16Layout {
     static constexpr uint64_t TILE = (uint64_t)THREADS * UPT;
     static constexpr int STAGE_UNITS = (int)TILE + 2 * HALO16;
     static constexpr uint32_t STAGE_BYTES = (uint32_t)STAGE_UNITS * 2;
-    static constexpr uint32_t OUT_WORDS = (uint32_t)((3 * TILE + 32) / 4);   /* staging, plus slack */
+    /* a warp's staging area: at most 3 bytes a unit, plus 1 when the warp's
+     * units end inside a pair, from the 16-byte phase (0..15) of its address */
+    static constexpr uint32_t WARP_OUT = (uint32_t)((3 * 32 * UPT + 1 + 15 + 15) / 16 * 16);
+    static constexpr uint32_t OUT_WORDS = (uint32_t)(THREADS / 32) * WARP_OUT / 4;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)OUT_WORDS * 4;
-    static_assert(STAGE_BYTES % 16 == 0 && OUT_WORDS % 4 == 0, "16-byte granules");
+    static_assert(STAGE_BYTES % 16 == 0 && WARP_OUT % 16 == 0, "16-byte granules");
 };
 
 /*
@@ -213,7 +216,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     extern __shared__ uint4 smem4[];
     uint16_t *stages = reinterpret_cast<uint16_t *>(smem4);
     uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
-    uint32_t *outw = reinterpret_cast<uint32_t *>(outw4);
     uint8_t *outb = reinterpret_cast<uint8_t *>(outw4);
     __shared__ unsigned long long s_bar[STAGES];
     __shared__ unsigned long long s_ring[STAGES];
@@ -371,72 +373,13 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
                 w[4 * v + 3] = units_of<BE>(q.w);
             }
             const uint32_t nu = unit_of<BE>(sb[i0 + UPT]);
-            /* each unit's bytes, at offsets from the tile's first output byte.
-             * Uniform-class fast paths: when every unit of every thread of
-             * the warp takes 3 bytes (BMP from U+0800, no surrogate), or 1,
-             * or 2, the bytes go to fixed offsets with no per-unit length
-             * work (the same bytes the general path writes). */
-            uint32_t len_and = c_len[0], len_or = c_len[0];
-#pragma unroll
-            for (int j = 1; j < NL; j++) {
-                len_and &= c_len[j];
-                len_or |= c_len[j];
-            }
-            if (__all_sync(FULL_MASK, len_and == 0x03030303u && len_or == 0x03030303u)) {
-                uint8_t *dst = outb + c_end - 3 * UPT;
-#pragma unroll
-                for (int k = 0; k < UPT; k++) {
-                    const uint32_t u = UNIT(k);
-                    dst[3 * k] = (uint8_t)(0xE0 | (u >> 12));
-                    dst[3 * k + 1] = (uint8_t)(0x80 | ((u >> 6) & 0x3F));
-                    dst[3 * k + 2] = (uint8_t)(0x80 | (u & 0x3F));
-                }
-            } else if (__all_sync(FULL_MASK, len_and == 0x01010101u && len_or == 0x01010101u)) {
-                uint8_t *dst = outb + c_end - UPT;
-#pragma unroll
-                for (int k = 0; k < UPT; k++) dst[k] = (uint8_t)UNIT(k);
-            } else if (__all_sync(FULL_MASK, len_and == 0x02020202u && len_or == 0x02020202u)) {
-                uint8_t *dst = outb + c_end - 2 * UPT;
-#pragma unroll
-                for (int k = 0; k < UPT; k++) {
-                    const uint32_t u = UNIT(k);
-                    dst[2 * k] = (uint8_t)(0xC0 | (u >> 6));
-                    dst[2 * k + 1] = (uint8_t)(0x80 | (u & 0x3F));
-                }
-            } else if (c_whole) {
-                /* every unit of the tile is inside the input: units 3.. go
-                 * back to front with unconditional stores, then units 2, 1, 0
-                 * exactly.  The strays stay inside the thread's run because
-                 * units 0-3 take at least 3 bytes: only the low half of a
-                 * pair takes none, and if that is unit 1, 2 or 3, its high
-                 * half is unit 0, 1 or 2 and takes 4. */
-                uint32_t e = smem_u32(outb) + c_end;
-#pragma unroll
-                for (int k = UPT - 1; k >= 3; k--)
-                    e = put_utf8_back(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu,
-                                      byte_at(c_len[k / 4], k % 4));
-#pragma unroll
-                for (int k = 2; k >= 0; k--) {
-                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
-                    e -= l;
-                    put_utf8(e, UNIT(k), UNIT(k + 1), l);
-                }
-            } else {
-                uint32_t e = smem_u32(outb) + c_end;
-#pragma unroll
-                for (int k = UPT - 1; k >= 0; k--) {
-                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
-                    e -= l;
-                    put_utf8(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
-                }
-            }
-
             /* c's exclusive output offset, by warp 0 alone: its window (the
-             * 32 tiles before c, requested at the top of the iteration) is
-             * usable when an inclusive prefix appears in it and every entry
-             * before that one has been published; otherwise the warp walks
-             * back, waiting (bounded) for each word.  The barrier then marks
-             * the staging buffer complete and hands G0 to every thread. */
+             * 32 tiles before c, requested at the top of the iteration, so
+             * its words have arrived while phase A of n ran) is usable when an
+             * inclusive prefix appears in it and every entry before that one
+             * has been published; otherwise the warp walks back, waiting
+             * (bounded) for each word.  The barrier then hands G0 to every
+             * thread (all of them have read c's stage by then). */
             if (c_tile > 0 && wid == 0) {
                 const bool in_window = lb_idx >= 0;
                 const uint64_t flag = in_window ? ((lb_word >> 40) & 3) : ST_PREFIX;
@@ -461,40 +404,95 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
              * flight close together, so look-backs seldom wait) */
             if (tid == 0 && have_n) issue(atomicAdd(&hdr->ticket, 1ull), c_stage);
 
-            /* write the tile's output bytes [G0, G0 + cnt), clipped to the
-             * capacity: aligned 16-byte stores, each assembled from the
-             * staging words by funnel shifts when the destination is not
-             * aligned like the staging buffer */
-            const uint64_t cnt = G0 >= cap ? 0 : (G0 + c_total > cap ? cap - G0 : c_total);
-            const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
-            uint8_t *gbase = out + G0 - shift;      /* 16-byte aligned; byte j <-> staging byte j - shift */
-            const uint32_t lim = shift + (uint32_t)cnt;
-            const uint32_t vf = shift ? 1u : 0u, vl = lim >> 4;   /* the whole vectors: [vf, vl) */
-            const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
-            if (r8 == 0) {
-                for (uint32_t i = vf + tid; i < vl; i += THREADS) {
-                    const uint32_t j = 4 * i - q;
-                    st_stream16(gbase + 16 * i, make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]));
+            /* this warp's part of the tile's output, bytes [ws, we) from the
+             * tile's first byte, is staged in the warp's own area at the
+             * 16-byte phase of its global address, so that it leaves as whole
+             * 16-byte vectors copied as they are (plus at most 15 bytes at
+             * each end), without waiting for the other warps */
+            uint32_t own = 0;
+#pragma unroll
+            for (int j = 0; j < NL; j++) own += byte_sum(c_len[j]);
+            const uint32_t ws = __shfl_sync(FULL_MASK, c_end - own, 0), we = __shfl_sync(FULL_MASK, c_end, 31);
+            const uint32_t a = (uint32_t)(((uintptr_t)out + G0 + ws) & 15);
+            uint8_t *wb = outb + (size_t)wid * Lay::WARP_OUT;
+            const uint32_t cpos = a + (c_end - ws);   /* end of this thread's bytes in the warp's area */
+            /* each unit's bytes, in this warp's staging area.
+             * Uniform-class fast paths: when every unit of every thread of
+             * the warp takes 3 bytes (BMP from U+0800, no surrogate), or 1,
+             * or 2, the bytes go to fixed offsets with no per-unit length
+             * work (the same bytes the general path writes). */
+            uint32_t len_and = c_len[0], len_or = c_len[0];
+#pragma unroll
+            for (int j = 1; j < NL; j++) {
+                len_and &= c_len[j];
+                len_or |= c_len[j];
+            }
+            if (__all_sync(FULL_MASK, len_and == 0x03030303u && len_or == 0x03030303u)) {
+                uint8_t *dst = wb + cpos - 3 * UPT;
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    dst[3 * k] = (uint8_t)(0xE0 | (u >> 12));
+                    dst[3 * k + 1] = (uint8_t)(0x80 | ((u >> 6) & 0x3F));
+                    dst[3 * k + 2] = (uint8_t)(0x80 | (u & 0x3F));
+                }
+            } else if (__all_sync(FULL_MASK, len_and == 0x01010101u && len_or == 0x01010101u)) {
+                uint8_t *dst = wb + cpos - UPT;
+#pragma unroll
+                for (int k = 0; k < UPT; k++) dst[k] = (uint8_t)UNIT(k);
+            } else if (__all_sync(FULL_MASK, len_and == 0x02020202u && len_or == 0x02020202u)) {
+                uint8_t *dst = wb + cpos - 2 * UPT;
+#pragma unroll
+                for (int k = 0; k < UPT; k++) {
+                    const uint32_t u = UNIT(k);
+                    dst[2 * k] = (uint8_t)(0xC0 | (u >> 6));
+                    dst[2 * k + 1] = (uint8_t)(0x80 | (u & 0x3F));
+                }
+            } else if (c_whole) {
+                /* every unit of the tile is inside the input: units 3.. go
+                 * back to front with unconditional stores, then units 2, 1, 0
+                 * exactly.  The strays stay inside the thread's run because
+                 * units 0-3 take at least 3 bytes: only the low half of a
+                 * pair takes none, and if that is unit 1, 2 or 3, its high
+                 * half is unit 0, 1 or 2 and takes 4. */
+                uint32_t e = smem_u32(wb) + cpos;
+#pragma unroll
+                for (int k = UPT - 1; k >= 3; k--)
+                    e = put_utf8_back(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu,
+                                      byte_at(c_len[k / 4], k % 4));
+#pragma unroll
+                for (int k = 2; k >= 0; k--) {
+                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
+                    e -= l;
+                    put_utf8(e, UNIT(k), UNIT(k + 1), l);
                 }
             } else {
-                for (uint32_t i = vf + tid; i < vl; i += THREADS) {
-                    const uint32_t j = 4 * i - q;   /* >= 1: vf = 1 */
-                    const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
-                    st_stream16(gbase + 16 * i,
-                                make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
-                                           __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8)));
+                uint32_t e = smem_u32(wb) + cpos;
+#pragma unroll
+                for (int k = UPT - 1; k >= 0; k--) {
+                    const uint32_t l = byte_at(c_len[k / 4], k % 4);
+                    e -= l;
+                    put_utf8(e, UNIT(k), k + 1 < UPT ? UNIT(k + 1) : nu, l);
                 }
             }
-            {   /* the partial vectors at the two ends, a byte per thread of the last warp */
-                const uint32_t head_end = 16 * vf < lim ? 16 * vf : lim;         /* bytes [shift, head_end) */
-                const uint32_t tail_start = 16 * vl > head_end ? 16 * vl : head_end;   /* [tail_start, lim) */
-                const int t = tid - (THREADS - 32);
-                if (t >= 0 && t < 16) {
-                    const uint32_t b = shift + (uint32_t)t;
-                    if (b < head_end) gbase[b] = outb[b - shift];
-                } else if (t >= 16) {
-                    const uint32_t b = tail_start + (uint32_t)(t - 16);
-                    if (b < lim) gbase[b] = outb[b - shift];
+
+            __syncwarp();
+            {   /* write-out of [G0 + ws, G0 + we), clipped to the capacity */
+                const uint64_t g = G0 + ws;
+                const uint64_t cnt = g >= cap ? 0 : (g + (we - ws) > cap ? cap - g : (uint64_t)(we - ws));
+                uint8_t *gbase = out + g - a;   /* 16-byte aligned; global byte j <-> staged byte j */
+                const uint32_t lim = a + (uint32_t)cnt;
+                const uint32_t vf = a ? 1u : 0u, vl = lim >> 4;   /* the whole vectors: [vf, vl) */
+                for (uint32_t i = vf + lane; i < vl; i += 32)
+                    st_stream16(gbase + 16 * i, *reinterpret_cast<const uint4 *>(wb + 16 * i));
+                const uint32_t head_end = a ? (16 < lim ? 16u : lim) : 0u;          /* bytes [a, head_end) */
+                const uint32_t tail_start = 16 * vl > head_end ? 16 * vl : head_end;   /* bytes [tail_start, lim) */
+                if (lane < 16) {
+                    const uint32_t b = a + (uint32_t)lane;
+                    if (b < head_end) gbase[b] = wb[b];
+                } else {
+                    const uint32_t b = tail_start + (uint32_t)(lane - 16);
+                    if (b < lim) gbase[b] = wb[b];
                 }
             }
 
@@ -504,9 +502,6 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
             if (G0 <= cap && G0 + c_total > cap) {
                 const long long e0 = (long long)(c_tile * TILE + (uint64_t)tid * UPT);
                 uint64_t cap_first = NONE;
-                uint32_t own = 0;
-#pragma unroll
-                for (int j = 0; j < NL; j++) own += byte_sum(c_len[j]);
                 uint64_t g = G0 + c_end - own;
 #pragma unroll
                 for (int k = 0; k < UPT; k++) {

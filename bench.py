@@ -417,6 +417,8 @@ def run_gpu(args):
         "gchar_s": world * args.steps * chars / (region_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "traffic_note": ("steady-state DRAM bytes per launch: one ncu launch of the 128 MiB case "
+                                      "with --cache-control none, times 2") if traffic else None,
                      "algorithmic_bytes": int(algo_bytes), "kernel": KERNEL,
                      "avg_launch_us": avg_launch_s * 1e6, "peak_source": peak_kind},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(data.nbytes),

@@ -305,13 +305,82 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     }
                 }
             } else {
-                /* one bit per character start of the chunk; each step reads the
-                 * four bytes at the start from the stage */
+                /* one bit per character start of the chunk */
                 uint32_t lm = 0;
 #pragma unroll
                 for (int k = 0; k < WORDS; k++)
                     lm |= ((((lead[k] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
                 const uint8_t *row = sb + i0;
+                /* Uniform-pattern paths (Section 4, the fast paths in front of
+                 * Algorithm 2: a block of 2-byte characters only, or of 3-byte
+                 * characters only).  A chunk qualifies when no byte is ASCII,
+                 * its leads come every other byte with none from 0xE0 (2-byte
+                 * characters), or every third byte all in E0-EF (3-byte
+                 * characters); it then holds exactly the characters those
+                 * leads start, the last one ending in the bytes after the
+                 * chunk.  Warp-uniform: a warp takes a path only when all its
+                 * threads qualify. */
+                bool two = c_interior && (lm == 0x55555555u || lm == 0xAAAAAAAAu);
+                bool three = c_interior && (lm == 0x49249249u || lm == 0x92492492u || lm == 0x24924924u);
+                const bool try_two = __all_sync(FULL_MASK, two), try_three = __all_sync(FULL_MASK, three);
+                if (try_two || try_three) {   /* the bytes, only where the leads already fit a pattern */
+                    uint32_t all = 0xFFFFFFFFu, e0 = 0, f0 = 0, lead_lt_e0 = 0;
+#pragma unroll
+                    for (int k = 0; k < WORDS; k++) {
+                        const uint32_t x = w[k];
+                        const uint32_t ge_e0 = x & (x << 1) & (x << 2) & 0x80808080u;
+                        all &= x;
+                        e0 |= ge_e0;
+                        f0 |= ge_e0 & (x << 3);
+                        lead_lt_e0 |= lead[k] & ~ge_e0;
+                    }
+                    const bool no_ascii = (all & 0x80808080u) == 0x80808080u;
+                    two = two && no_ascii && e0 == 0;
+                    three = three && no_ascii && f0 == 0 && lead_lt_e0 == 0;
+                }
+                if (try_two && __all_sync(FULL_MASK, two)) {
+                    /* 16 characters: four bytes lead, continuation, lead,
+                     * continuation give two units, 110xxxxx 10yyyyyy -> x:y */
+                    const uint32_t wn = *reinterpret_cast<const uint32_t *>(row + BPT);
+                    const uint32_t r8 = (lm & 1u) ? 0u : 8u;   /* leads at odd bytes: windows one byte on */
+#pragma unroll
+                    for (int k = 0; k < WORDS; k++) {
+                        const uint32_t x = __funnelshift_r(w[k], k + 1 < WORDS ? w[k + 1] : wn, r8);
+                        const uint32_t u2 = ((x & 0x001F001Fu) << 6) | ((x >> 8) & 0x003F003Fu);
+                        out16[o + 2 * k] = (uint16_t)u2;
+                        out16[o + 2 * k + 1] = (uint16_t)(u2 >> 16);
+                    }
+                    lm = 0;
+                } else if (try_three && __all_sync(FULL_MASK, three)) {
+                    /* 10 or 11 characters from the first lead r (0, 1 or 2):
+                     * each 12 bytes from r + 12m hold four, 1110xxxx 10yyyyyy
+                     * 10zzzzzz -> x:y:z */
+                    const uint32_t wn0 = *reinterpret_cast<const uint32_t *>(row + BPT);
+                    const uint32_t wn1 = *reinterpret_cast<const uint32_t *>(row + BPT + 4);
+                    const uint32_t r = (lm & 1u) ? 0u : ((lm & 2u) ? 1u : 2u);
+                    const uint32_t nc = __popc(lm);
+                    uint32_t ww[WORDS + 2];
+#pragma unroll
+                    for (int k = 0; k < WORDS; k++) ww[k] = w[k];
+                    ww[WORDS] = wn0;
+                    ww[WORDS + 1] = wn1;
+#pragma unroll
+                    for (int m = 0; m < (BPT + 11) / 12; m++) {
+                        const uint32_t x0 = __funnelshift_r(ww[3 * m], ww[3 * m + 1], 8 * r);
+                        const uint32_t x1 = __funnelshift_r(ww[3 * m + 1], ww[3 * m + 2], 8 * r);
+                        const uint32_t x2 = __funnelshift_r(ww[3 * m + 2], ww[3 * m + 3], 8 * r);
+                        const uint32_t cs[4] = {x0, __funnelshift_r(x0, x1, 24), __funnelshift_r(x1, x2, 16), x2 >> 8};
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const uint32_t c = cs[j];
+                            const uint32_t u = ((c & 0x0Fu) << 12) | ((c >> 2) & 0x0FC0u) | ((c >> 16) & 0x3Fu);
+                            if (4 * m + j < (int)nc) out16[o + 4 * m + j] = (uint16_t)u;
+                        }
+                    }
+                    lm = 0;
+                }
+                /* the rest: each step reads the four bytes at a character
+                 * start from the stage */
                 while (lm) {
                     const int p = __ffs(lm) - 1;
                     lm &= lm - 1;

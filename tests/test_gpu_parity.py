@@ -448,3 +448,51 @@ def test_uniform_and_mixed_warps_in_one_tile(g, ws):
     d[3001] = 0xD800
     check_16to8(g, ws, d)
     check_16to8(g, ws, d, cap=2500)
+
+
+def test_uniform_two_and_three_byte_warps_utf8(g, ws):
+    """UTF-8 -> UTF-16 warps whose chunks hold only 2-byte or only 3-byte
+    characters take the uniform-pattern paths (leads every other or every
+    third byte); covered at every start phase of the characters against the
+    chunks, with one character of another length planted in one thread's
+    chunk (the warp falls back), and with errors inside uniform runs (an
+    overlong 2-byte lead, an encoded surrogate, a 3-byte character cut short
+    at a chunk's end, a stray continuation)."""
+    rng = np.random.default_rng(7)
+    two = np.array([0xC0 | (c >> 6) for c in range(0x400, 0x500)], np.uint8)
+    for script, length in ((W.SCRIPT_TWO_BYTE, 2), (W.SCRIPT_CJK, 3)):
+        base = W.utf8_text(11 * length, 5 * TILE8 + 777, script)
+        for lead_bytes in range(0, 6):           # 0-5 ASCII bytes shift the character phase
+            data = np.concatenate([np.full(lead_bytes, 0x41, np.uint8), base])
+            check_8to16(g, ws, data)
+            check_8to16(g, ws, data, in_off=lead_bytes % 3, out_off=lead_bytes % 2)
+            # one character of another length in the middle of a chunk
+            d2 = data.copy()
+            p = 2 * TILE8 + 96 * 32 + 7
+            p -= (p - lead_bytes) % length
+            d2 = np.concatenate([d2[:p], np.array([0x41], np.uint8), d2[p:]])
+            check_8to16(g, ws, d2)
+        # errors inside a uniform run, near chunk (32-byte) and tile ends
+        for at in (TILE8 - 3, TILE8 - 1, 3 * TILE8 + 32 * 17 + 1, 4 * TILE8 + 31):
+            q = at - at % length                      # a character start (no ASCII prefix)
+            for kind in range(4):
+                bad = base.copy()
+                if kind == 0:
+                    bad[q] = 0xC1 if length == 2 else 0xE0   # overlong lead (E0 then 80-9F only if the next byte is low)
+                    if length == 3:
+                        bad[q + 1] = 0x80 | (bad[q + 1] & 0x1F)
+                elif kind == 1:
+                    if length == 3:
+                        bad[q], bad[q + 1] = 0xED, 0xA0 | (bad[q + 1] & 0x1F)   # U+D800-DFFF
+                    else:
+                        bad[q + 1] = 0x41                                     # 2-byte lead cut short
+                elif kind == 2:
+                    bad = bad[:q + length - 1]                                # cut short at the end
+                else:
+                    bad[q] = 0x80 | (bad[q] & 0x3F)                           # stray continuation
+                check_8to16(g, ws, bad)
+    # random 2-byte text with random planted ASCII bytes, many sizes
+    for n in rng.integers(1, 3 * TILE8, 12):
+        t = W.utf8_text(int(n), int(n), W.SCRIPT_TWO_BYTE).copy()
+        t[rng.integers(0, t.size, 2)] = 0x20
+        check_8to16(g, ws, t)

@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "utf8_dfa.h"
 
 namespace gputf {
 
@@ -558,6 +559,39 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
 /* Streaming passes: a grid of resident CTAs walks the tiles (grid-stride);
  * each thread issues the loads of its chunk of the next tile before working
  * on the current one, and no barrier is taken per tile. */
+
+/* The validate-only pass runs the automaton of utf8_dfa.h over each byte:
+ * a byte's class, then the next state, both looked up in shared memory.
+ * Each table is kept once per bank: entry e sits in word 32 e + lane, so
+ * the 32 lanes of a warp read 32 different banks whatever they look up.
+ * Class entries hold the class times 128 and transition entries the next
+ * state times 128 * classes, byte offsets into the transition table, so a
+ * step is a shift and a mask for the byte, two loads and one add. */
+constexpr uint32_t DFA_ROW = 128;                                            /* 32 lanes x 4 bytes */
+constexpr uint32_t DFA_CLASS_BYTES = 256 * DFA_ROW;
+constexpr uint32_t DFA_STATE_STRIDE = GPUTF_DFA_CLASSES * DFA_ROW;
+constexpr uint32_t DFA_SMEM = DFA_CLASS_BYTES + GPUTF_DFA_STATES * DFA_STATE_STRIDE;
+
+template <int THREADS>
+__device__ __forceinline__ void dfa_tables(uint32_t *t)
+{
+    for (uint32_t i = threadIdx.x; i < 256 * 32; i += THREADS) t[i] = gputf_dfa_class(i >> 5) * DFA_ROW;
+    uint32_t *nt = t + DFA_CLASS_BYTES / 4;
+    for (uint32_t i = threadIdx.x; i < GPUTF_DFA_STATES * GPUTF_DFA_CLASSES * 32; i += THREADS) {
+        const uint32_t e = i >> 5;
+        nt[i] = gputf_dfa_next(e / GPUTF_DFA_CLASSES, e % GPUTF_DFA_CLASSES) * DFA_STATE_STRIDE;
+    }
+}
+
+/* One step: the state offset after byte j of word w. */
+template <int J>
+__device__ __forceinline__ uint32_t dfa_step(const char *tab, uint32_t sv, uint32_t w, uint32_t lane4)
+{
+    const uint32_t boff = (J == 0 ? (w << 7) : (w >> (8 * J - 7))) & 0x7F80u;   /* byte * 128 */
+    const uint32_t cls = *reinterpret_cast<const uint32_t *>(tab + (boff | lane4));
+    return *reinterpret_cast<const uint32_t *>(tab + DFA_CLASS_BYTES + sv + cls + lane4);
+}
+
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles, WsHeader *hdr,
@@ -565,59 +599,106 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
 {
     constexpr int BPT = 4 * WORDS;
     constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
+    constexpr uint32_t SV_REJECT = GPUTF_DFA_REJECT * DFA_STATE_STRIDE;
+    extern __shared__ uint4 smem4[];
+    const char *tab = reinterpret_cast<const char *>(smem4);
     __shared__ unsigned long long s_min[THREADS / 32];
     __shared__ unsigned s_flag;
+    dfa_tables<THREADS>(reinterpret_cast<uint32_t *>(smem4));
+    __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t lane4 = 4u * (uint32_t)lane;
     const uint64_t head = (uintptr_t)in & 15;
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;
     uint64_t first_err = NONE;
     uint64_t tile = blockIdx.x;
     uint32_t w[WORDS];
-    bool interior = false;
-    /* lane 0 also needs the word before its chunk (another warp's): it is
-     * loaded with the chunk, one tile ahead like the rest */
-    uint32_t before = 0;
+    /* lane 0 also needs the word before its chunk and lane 31 the word
+     * after it (other warps'): loaded with the chunk, one tile ahead */
+    uint32_t side = 0;
+    auto side_word = [&](uint64_t e0) -> uint32_t {
+        if (lane == 0) return word_at(base, (long long)e0 - 4, head, endx);
+        if (lane == 31) return word_at(base, (long long)(e0 + BPT), head, endx);
+        return 0u;
+    };
     if (tile < tiles) {
-        interior = load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
-        if (lane == 0) before = word_at(base, (long long)(tile * TILE + (uint64_t)tid * BPT) - 4, head, endx);
+        load_chunk8<WORDS>(base, tile * TILE + (uint64_t)tid * BPT, head, endx, w);
+        side = side_word(tile * TILE + (uint64_t)tid * BPT);
     }
     while (tile < tiles) {
         const uint64_t e0 = tile * TILE + (uint64_t)tid * BPT;
         const uint64_t next = tile + gridDim.x;
-        uint32_t v[WORDS], v_before = 0;
-        bool v_interior = false;
+        uint32_t v[WORDS], v_side = 0;
         if (next < tiles) {
-            v_interior = load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
-            if (lane == 0) v_before = word_at(base, (long long)(next * TILE + (uint64_t)tid * BPT) - 4, head, endx);
+            load_chunk8<WORDS>(base, next * TILE + (uint64_t)tid * BPT, head, endx, v);
+            v_side = side_word(next * TILE + (uint64_t)tid * BPT);
         }
         uint32_t pw = __shfl_up_sync(FULL_MASK, w[WORDS - 1], 1);
-        if (lane == 0) pw = before;
+        uint32_t nw = __shfl_down_sync(FULL_MASK, w[0], 1);
+        if (lane == 0) pw = side;
+        if (lane == 31) nw = side;
         uint32_t any = pw;
 #pragma unroll
         for (int k = 0; k < WORDS; k++) any |= w[k];
-        /* all-ASCII chunks (and the word before them) hold no error */
+        /* all-ASCII chunks (and the bytes before them) hold no error */
         if ((any & 0x80808080u) != 0 && first_err == NONE) {
-            gputf_u8state st = gputf_u8state_of(pw);
-            uint32_t errs[WORDS], anyerr = 0;
+            /* the state at the chunk: the three bytes before it replayed
+             * from SYNC0; then every byte; then, while inside a character,
+             * up to three bytes after the chunk (bytes outside the input
+             * read as zero, so a character cut by the end rejects there) */
+            /* two independent runs, over the chunk's two halves, each
+             * resynchronised from the three bytes before it; the first runs
+             * on into the second half while inside a character */
+            constexpr int HW = WORDS / 2;
+            const uint32_t inside_lo = GPUTF_DFA_NEED1 * DFA_STATE_STRIDE;
+            const uint32_t inside_span = (GPUTF_DFA_AFTER_F4 - GPUTF_DFA_NEED1) * DFA_STATE_STRIDE;
+            uint32_t sa = GPUTF_DFA_SYNC0 * DFA_STATE_STRIDE, sb = sa;
+            sa = dfa_step<1>(tab, sa, pw, lane4);
+            sb = dfa_step<1>(tab, sb, w[HW - 1], lane4);
+            sa = dfa_step<2>(tab, sa, pw, lane4);
+            sb = dfa_step<2>(tab, sb, w[HW - 1], lane4);
+            sa = dfa_step<3>(tab, sa, pw, lane4);
+            sb = dfa_step<3>(tab, sb, w[HW - 1], lane4);
 #pragma unroll
-            for (int k = 0; k < WORDS; k++) {
-                errs[k] = gputf_utf8_errors_step(&st, w[k]);
-                anyerr |= errs[k];
+            for (int k = 0; k < HW; k++) {
+                sa = dfa_step<0>(tab, sa, w[k], lane4);
+                sb = dfa_step<0>(tab, sb, w[HW + k], lane4);
+                sa = dfa_step<1>(tab, sa, w[k], lane4);
+                sb = dfa_step<1>(tab, sb, w[HW + k], lane4);
+                sa = dfa_step<2>(tab, sa, w[k], lane4);
+                sb = dfa_step<2>(tab, sb, w[HW + k], lane4);
+                sa = dfa_step<3>(tab, sa, w[k], lane4);
+                sb = dfa_step<3>(tab, sb, w[HW + k], lane4);
             }
-            if (anyerr) {   /* the first flagged byte of the chunk */
-#pragma unroll
-                for (int k = WORDS - 1; k >= 0; k--) {
-                    uint32_t nz = gputf_nonzero_bytes(errs[k]);
-                    if (!interior) nz &= range_mask((long long)(e0 + 4 * k), head, endx, true);
-                    if (nz) first_err = e0 + 4 * k + first_byte(nz) - head;
+            if (sa - inside_lo <= inside_span) sa = dfa_step<0>(tab, sa, w[HW], lane4);
+            if (sb - inside_lo <= inside_span) sb = dfa_step<0>(tab, sb, nw, lane4);
+            if (sa - inside_lo <= inside_span) sa = dfa_step<1>(tab, sa, w[HW], lane4);
+            if (sb - inside_lo <= inside_span) sb = dfa_step<1>(tab, sb, nw, lane4);
+            if (sa - inside_lo <= inside_span) sa = dfa_step<2>(tab, sa, w[HW], lane4);
+            if (sb - inside_lo <= inside_span) sb = dfa_step<2>(tab, sb, nw, lane4);
+            if (sa == SV_REJECT || sb == SV_REJECT) {
+                /* rare: walk again, one byte at a time, to the first
+                 * rejected byte (a rejection while replaying the bytes
+                 * before the chunk counts at the chunk's first byte) */
+                uint32_t st = GPUTF_DFA_SYNC0;
+                int at = -1;
+                for (int i = -3; i < BPT + 3 && at < 0; i++) {
+                    const uint32_t word = i < 0 ? pw : (i < BPT ? w[(i >> 2) & (WORDS - 1)] : nw);
+                    const uint32_t b = (word >> (8 * ((i + 4) & 3))) & 0xFF;
+                    if (i >= BPT && !gputf_dfa_inside(st)) break;
+                    st = gputf_dfa_next(st, gputf_dfa_class(b));
+                    if (st == GPUTF_DFA_REJECT) at = i < 0 ? 0 : i;
+                }
+                if (at >= 0) {
+                    const uint64_t pos = e0 + (uint64_t)at - head;
+                    first_err = pos < n ? pos : n;
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < WORDS; k++) w[k] = v[k];
-        interior = v_interior;
-        before = v_before;
+        side = v_side;
         tile = next;
     }
     if (__syncthreads_or(first_err != NONE)) {
@@ -638,8 +719,6 @@ validate_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
     reset_workspace(hdr, nullptr, 0);
 }
 
-/* UTF-16 length of UTF-8 input (Table 2): one unit per byte that is not a
- * continuation byte, one more per byte >= 0xF0. */
 template <int THREADS, int WORDS>
 __global__ void __launch_bounds__(THREADS)
 utf16_length_from_utf8_kernel(const uint8_t *__restrict__ in, uint64_t n, uint64_t tiles,
@@ -760,8 +839,15 @@ cudaError_t launch_validate_utf8(const uint8_t *in, uint64_t n, void *ws, DevRes
     const uint64_t tiles = ((uintptr_t)in % 16 + n + 1 + TILE - 1) / TILE;
     static int per_sm = 0;
     auto kern = validate_utf8_kernel<T, W>;
-    kern<<<resident_grid8(kern, T, tiles, sms, &per_sm), T, 0, stream>>>(in, n, tiles, static_cast<WsHeader *>(ws),
-                                                                          res);
+    if (per_sm == 0) {   /* the automaton's tables take more than the default 48 KiB of shared memory */
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DFA_SMEM);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, T, DFA_SMEM) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    kern<<<resident_grid8(kern, T, tiles, sms, &per_sm), T, DFA_SMEM, stream>>>(in, n, tiles,
+                                                                                 static_cast<WsHeader *>(ws), res);
     return cudaGetLastError();
 }
 

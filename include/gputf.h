@@ -254,8 +254,10 @@ typedef struct gputf_batch {
  * direction (UTF-8 -> UTF-16, then UTF-16 -> UTF-8). */
 size_t gputf_batch_workspace_bytes(uint64_t units8, uint64_t count8, uint64_t units16, uint64_t count16);
 
-/* Number of tile configurations gputf_batch_transcode accepts (0 .. n-1);
- * an autotuner picks one per input mix. */
+/* Number of tile configurations gputf_batch_transcode accepts (0 .. n-1):
+ * threads and units per thread, each either one CTA per tile or a
+ * persistent grid of resident CTAs taking tiles until none is left; an
+ * autotuner picks one per input mix. */
 int gputf_batch_config_count(void);
 
 /* Batched validating transcoding of many strings in one launch (the paper's

@@ -731,27 +731,44 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
 
 /* ------------------------------------------------------------------------
  * The batched kernel: tickets [0, d8.tiles) are UTF-8 tiles, the rest
- * UTF-16 tiles.  One tile per CTA, taken in ticket order.
+ * UTF-16 tiles, taken in ticket order.  Two forms: one tile per CTA (the
+ * hardware's block scheduler hands out the CTAs), or persistent (a grid of
+ * resident CTAs, each taking tickets until none is left).  Either way a
+ * CTA waits only for tiles of smaller tickets, which running CTAs hold.
  * ---------------------------------------------------------------------- */
-template <int THREADS, int UPT8, int UPT16>
+template <int THREADS, int UPT8, int UPT16, bool PERSIST>
 __global__ void __launch_bounds__(THREADS)
 batch_kernel(BatchDir d8, BatchDir d16, WsHeader *hdr, unsigned long long *ws_words, uint64_t ws_nwords)
 {
-    constexpr uint64_t TILE8 = (uint64_t)THREADS * UPT8, TILE16 = (uint64_t)THREADS * UPT16;
     __shared__ BatchShared sm;
     __shared__ unsigned s_tile_flag;
     __shared__ unsigned long long s_ticket;
     extern __shared__ uint4 smem4[];
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&hdr->ticket, 1ull);
-    __syncthreads();
     const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
-    const uint64_t t = s_ticket;
-    if (t < d8.tiles)
-        batch8_tile<THREADS, UPT8>(d8, t, epoch, hdr, sm, reinterpret_cast<uint8_t *>(smem4));
-    else if (t - d8.tiles < d16.tiles)
-        batch16_tile<THREADS, UPT16>(d16, t - d8.tiles, epoch, hdr, sm, reinterpret_cast<uint16_t *>(smem4));
-    (void)TILE8;
-    (void)TILE16;
+    if constexpr (!PERSIST) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&hdr->ticket, 1ull);
+        __syncthreads();
+        const uint64_t t = s_ticket;
+        if (t < d8.tiles)
+            batch8_tile<THREADS, UPT8>(d8, t, epoch, hdr, sm, reinterpret_cast<uint8_t *>(smem4));
+        else if (t - d8.tiles < d16.tiles)
+            batch16_tile<THREADS, UPT16>(d16, t - d8.tiles, epoch, hdr, sm, reinterpret_cast<uint16_t *>(smem4));
+    } else {
+        for (;;) {
+            if (threadIdx.x == 0) s_ticket = atomicAdd(&hdr->ticket, 1ull);
+            __syncthreads();
+            const uint64_t t = s_ticket;
+            if (t < d8.tiles)
+                batch8_tile<THREADS, UPT8>(d8, t, epoch, hdr, sm, reinterpret_cast<uint8_t *>(smem4));
+            else if (t - d8.tiles < d16.tiles)
+                batch16_tile<THREADS, UPT16>(d16, t - d8.tiles, epoch, hdr, sm,
+                                             reinterpret_cast<uint16_t *>(smem4));
+            else
+                break;   /* every thread read the same ticket */
+            /* the tile functions end with a barrier: every thread has read
+             * s_ticket before thread 0 takes the next one */
+        }
+    }
     if (!finish_cta(hdr, &s_tile_flag)) return;
     reset_workspace(hdr, ws_words, ws_nwords);
 }
@@ -759,7 +776,7 @@ batch_kernel(BatchDir d8, BatchDir d16, WsHeader *hdr, unsigned long long *ws_wo
 /* ------------------------------------------------------------------------
  * Launch: configurations chosen by the autotuner, by index.
  * ---------------------------------------------------------------------- */
-template <int T, int U8, int U16>
+template <int T, int U8, int U16, bool PERSIST>
 static cudaError_t launch_cfg(const BatchDir &a8, const BatchDir &a16, void *ws, uint64_t ws_nwords,
                               cudaStream_t stream)
 {
@@ -773,27 +790,44 @@ static cudaError_t launch_cfg(const BatchDir &a8, const BatchDir &a16, void *ws,
     d16.status = d8.status + d8.tiles;
     d8.errw = d16.status + d16.tiles;
     d16.errw = d8.errw + d8.count;
-    const uint64_t grid = d8.tiles + d16.tiles;
+    uint64_t grid = d8.tiles + d16.tiles;
     if (grid == 0) return cudaSuccess;
     const size_t smem = ((uint64_t)T * U16 + 16) * 2 > (uint64_t)T * U8 + 32 ? ((uint64_t)T * U16 + 16) * 2
                                                                              : (uint64_t)T * U8 + 32;
-    batch_kernel<T, U8, U16><<<(unsigned)grid, T, smem, stream>>>(d8, d16, static_cast<WsHeader *>(ws), words,
-                                                                   ws_nwords);
+    auto kern = batch_kernel<T, U8, U16, PERSIST>;
+    if (PERSIST) {   /* the CTAs that fit on the device at once */
+        static int resident = 0;   /* per configuration (a template instance); same for every sm_103 device */
+        if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+            if (e != cudaSuccess) return e;
+            resident = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        if (grid > (uint64_t)resident) grid = (uint64_t)resident;
+    }
+    kern<<<(unsigned)grid, T, smem, stream>>>(d8, d16, static_cast<WsHeader *>(ws), words, ws_nwords);
     return cudaGetLastError();
 }
 
-int batch_config_count() { return 4; }
+int batch_config_count() { return 8; }
 
 uint64_t batch_min_tile_units() { return 128 * 8; }
 
 cudaError_t launch_batch(int cfg, const BatchDir &d8, const BatchDir &d16, void *ws, uint64_t ws_nwords,
                          cudaStream_t stream)
 {
+    /* 0-3: one tile per CTA; 4-7: the same shapes, persistent */
     switch (cfg) {
-    case 0: return launch_cfg<256, 16, 16>(d8, d16, ws, ws_nwords, stream);
-    case 1: return launch_cfg<256, 8, 8>(d8, d16, ws, ws_nwords, stream);
-    case 2: return launch_cfg<128, 16, 16>(d8, d16, ws, ws_nwords, stream);
-    case 3: return launch_cfg<128, 8, 8>(d8, d16, ws, ws_nwords, stream);
+    case 0: return launch_cfg<256, 16, 16, false>(d8, d16, ws, ws_nwords, stream);
+    case 1: return launch_cfg<256, 8, 8, false>(d8, d16, ws, ws_nwords, stream);
+    case 2: return launch_cfg<128, 16, 16, false>(d8, d16, ws, ws_nwords, stream);
+    case 3: return launch_cfg<128, 8, 8, false>(d8, d16, ws, ws_nwords, stream);
+    case 4: return launch_cfg<256, 16, 16, true>(d8, d16, ws, ws_nwords, stream);
+    case 5: return launch_cfg<256, 8, 8, true>(d8, d16, ws, ws_nwords, stream);
+    case 6: return launch_cfg<128, 16, 16, true>(d8, d16, ws, ws_nwords, stream);
+    case 7: return launch_cfg<128, 8, 8, true>(d8, d16, ws, ws_nwords, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -776,10 +776,16 @@ batch_kernel(BatchDir d8, BatchDir d16, WsHeader *hdr, unsigned long long *ws_wo
 /* ------------------------------------------------------------------------
  * Launch: configurations chosen by the autotuner, by index.
  * ---------------------------------------------------------------------- */
+/* The workspace holds one status word per tile, counted for tiles of this
+ * many units (gputf_batch_workspace_bytes): no shape may have smaller ones. */
+constexpr uint64_t BATCH_MIN_TILE_UNITS = 128 * 8;
+
 template <int T, int U8, int U16, bool PERSIST>
 static cudaError_t launch_cfg(const BatchDir &a8, const BatchDir &a16, void *ws, uint64_t ws_nwords,
                               cudaStream_t stream)
 {
+    static_assert((uint64_t)T * U8 >= BATCH_MIN_TILE_UNITS && (uint64_t)T * U16 >= BATCH_MIN_TILE_UNITS,
+                  "tiles smaller than the workspace sizing assumes");
     BatchDir d8 = a8, d16 = a16;
     d8.tiles = (d8.units + (uint64_t)T * U8 - 1) / ((uint64_t)T * U8);
     d16.tiles = (d16.units + (uint64_t)T * U16 - 1) / ((uint64_t)T * U16);
@@ -811,14 +817,15 @@ static cudaError_t launch_cfg(const BatchDir &a8, const BatchDir &a16, void *ws,
     return cudaGetLastError();
 }
 
-int batch_config_count() { return 8; }
+int batch_config_count() { return 18; }
 
-uint64_t batch_min_tile_units() { return 128 * 8; }
+uint64_t batch_min_tile_units() { return BATCH_MIN_TILE_UNITS; }
 
 cudaError_t launch_batch(int cfg, const BatchDir &d8, const BatchDir &d16, void *ws, uint64_t ws_nwords,
                          cudaStream_t stream)
 {
-    /* 0-3: one tile per CTA; 4-7: the same shapes, persistent */
+    /* threads x UTF-8 bytes x UTF-16 units per thread; 0-3, 8-9 and 12-14:
+     * one tile per CTA; 4-7, 10-11 and 15-17: the same shapes, persistent */
     switch (cfg) {
     case 0: return launch_cfg<256, 16, 16, false>(d8, d16, ws, ws_nwords, stream);
     case 1: return launch_cfg<256, 8, 8, false>(d8, d16, ws, ws_nwords, stream);
@@ -828,6 +835,16 @@ cudaError_t launch_batch(int cfg, const BatchDir &d8, const BatchDir &d16, void 
     case 5: return launch_cfg<256, 8, 8, true>(d8, d16, ws, ws_nwords, stream);
     case 6: return launch_cfg<128, 16, 16, true>(d8, d16, ws, ws_nwords, stream);
     case 7: return launch_cfg<128, 8, 8, true>(d8, d16, ws, ws_nwords, stream);
+    case 8: return launch_cfg<128, 32, 8, false>(d8, d16, ws, ws_nwords, stream);
+    case 9: return launch_cfg<64, 16, 16, false>(d8, d16, ws, ws_nwords, stream);
+    case 10: return launch_cfg<128, 32, 8, true>(d8, d16, ws, ws_nwords, stream);
+    case 11: return launch_cfg<64, 16, 16, true>(d8, d16, ws, ws_nwords, stream);
+    case 12: return launch_cfg<128, 32, 16, false>(d8, d16, ws, ws_nwords, stream);
+    case 13: return launch_cfg<256, 32, 8, false>(d8, d16, ws, ws_nwords, stream);
+    case 14: return launch_cfg<64, 32, 16, false>(d8, d16, ws, ws_nwords, stream);
+    case 15: return launch_cfg<128, 32, 16, true>(d8, d16, ws, ws_nwords, stream);
+    case 16: return launch_cfg<256, 32, 8, true>(d8, d16, ws, ws_nwords, stream);
+    case 17: return launch_cfg<64, 32, 16, true>(d8, d16, ws, ws_nwords, stream);
     default: return cudaErrorInvalidValue;
     }
 }

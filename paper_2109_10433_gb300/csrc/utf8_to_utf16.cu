@@ -98,12 +98,57 @@ __device__ __forceinline__ int first_byte(uint32_t m) { return (__ffs(m) - 8) >>
 
 constexpr int HALO8 = 16;   /* bytes staged on each side of a tile */
 
+/* Stores the four units a (units 0, 1) and b (units 2, 3) at unit index u of
+ * the staging buffer, in the widest stores that u's alignment allows (u is
+ * the same modulo 4 across the warp). */
+__device__ __forceinline__ void put_units4(uint16_t *o16, uint32_t u, uint32_t a, uint32_t b)
+{
+    if ((u & 3) == 0) {
+        *reinterpret_cast<uint2 *>(o16 + u) = make_uint2(a, b);
+    } else if ((u & 1) == 0) {
+        *reinterpret_cast<uint32_t *>(o16 + u) = a;
+        *reinterpret_cast<uint32_t *>(o16 + u + 2) = b;
+    } else {
+        o16[u] = (uint16_t)a;
+        o16[u + 1] = (uint16_t)(a >> 16);
+        o16[u + 2] = (uint16_t)b;
+        o16[u + 3] = (uint16_t)(b >> 16);
+    }
+}
+
+/* Stores the two units a (low half first) at unit index u. */
+__device__ __forceinline__ void put_units2(uint16_t *o16, uint32_t u, uint32_t a)
+{
+    if ((u & 1) == 0) {
+        *reinterpret_cast<uint32_t *>(o16 + u) = a;
+    } else {
+        o16[u] = (uint16_t)a;
+        o16[u + 1] = (uint16_t)(a >> 16);
+    }
+}
+
+/* The 16 bytes that start 2 S bytes before the end of the first of the two
+ * granules w[0..3], w[4..7]. */
+template <int S>
+__device__ __forceinline__ uint4 window16(const uint32_t (&w)[8])
+{
+    constexpr int b = 16 - 2 * S, k = b >> 2;
+    if constexpr ((b & 3) == 0) {
+        return make_uint4(w[k], w[k + 1], w[k + 2], w[k + 3]);
+    } else {
+        return make_uint4(__funnelshift_r(w[k], w[k + 1], 16), __funnelshift_r(w[k + 1], w[k + 2], 16),
+                          __funnelshift_r(w[k + 2], w[k + 3], 16), __funnelshift_r(w[k + 3], w[k + 4], 16));
+    }
+}
+
 template <int THREADS, int WORDS, int STAGES>
 struct U8Layout {
     static constexpr int BPT = 4 * WORDS;
     static constexpr uint64_t TILE = (uint64_t)THREADS * BPT;
     static constexpr uint32_t STAGE_BYTES = (uint32_t)TILE + 2 * HALO8;
-    static constexpr uint32_t OUT_BYTES = (uint32_t)(4 * TILE + 32);   /* up to 2 units per byte */
+    /* a thread's count is clamped to BPT + 1 units (see phase A) and its
+     * decoding writes at most 2 units a byte from there */
+    static constexpr uint32_t OUT_BYTES = (uint32_t)((2 * ((BPT + 1) * THREADS + 2 * BPT) + 15) / 16 * 16);
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + OUT_BYTES;
     static_assert(STAGE_BYTES % 16 == 0 && OUT_BYTES % 16 == 0, "16-byte granules");
 };
@@ -147,7 +192,6 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     extern __shared__ uint4 smem4[];
     uint8_t *stages = reinterpret_cast<uint8_t *>(smem4);
     uint4 *outw4 = smem4 + (size_t)STAGES * Lay::STAGE_BYTES / 16;
-    uint32_t *outw = reinterpret_cast<uint32_t *>(outw4);
     uint16_t *out16 = reinterpret_cast<uint16_t *>(outw4);
     uint8_t *outb = reinterpret_cast<uint8_t *>(outw4);
     __shared__ unsigned long long s_bar[STAGES];
@@ -237,6 +281,14 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                 }
                 n_total += __popc(lead) + __popc(f4);
             }
+            /* When a chunk's bytes up to its end are a prefix of valid UTF-8,
+             * every complete character gives at most one unit a byte and a
+             * 4-byte lead cut off by the chunk's end two for its one byte, so
+             * the chunk counts at most BPT + 1 units.  More means an error at
+             * or before the chunk's end, after which the output carries no
+             * meaning (and the result's `written` is recounted from the tiles
+             * before the error): the clamp bounds the staging buffer. */
+            if (n_total > (uint32_t)BPT + 1) n_total = (uint32_t)BPT + 1;
             /* validation, skipped by all-ASCII warps and all-ASCII threads */
             const bool ascii = (any & 0x80808080u) == 0;
             uint64_t first_err = NONE;
@@ -297,12 +349,30 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             /* decode at every lead into the staging buffer, in units from the
              * tile's first output unit (Section 3 bit arithmetic; Figs. 2-4) */
             uint32_t o = c_excl;
+            /* The all-ASCII and all-2-byte warp paths store cooperatively:
+             * in step i lane L takes the warp's word 32 i + L, so that a
+             * store instruction covers consecutive units instead of one unit
+             * in each lane's own stretch (lanes 8 or 16 words apart: 8- or
+             * 16-way bank conflicts).  The warp's units are consecutive from
+             * its lane 0's offset; stores are as wide as that offset's
+             * alignment allows. */
+            const uint32_t ow = __shfl_sync(FULL_MASK, o, 0);
+            const uint32_t *wsrc = reinterpret_cast<const uint32_t *>(sb + HALO8 + (size_t)wid * 32 * BPT);
             if (__all_sync(FULL_MASK, (any & 0x80808080u) == 0)) {
+                if (c_interior) {   /* every byte a character: unit ow + b for the warp's byte b */
 #pragma unroll
-                for (int k = 0; k < WORDS; k++) {
+                    for (int i = 0; i < WORDS; i++) {
+                        const uint32_t x = wsrc[32 * i + lane];
+                        const uint32_t u = ow + 128 * i + 4 * lane;
+                        put_units4(out16, u, __byte_perm(x, 0u, 0x4140), __byte_perm(x, 0u, 0x4342));
+                    }
+                } else {
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        if (lead[k] & (0x80u << (8 * j))) out16[o++] = (uint16_t)((w[k] >> (8 * j)) & 0xFF);
+                    for (int k = 0; k < WORDS; k++) {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            if (lead[k] & (0x80u << (8 * j))) out16[o++] = (uint16_t)((w[k] >> (8 * j)) & 0xFF);
+                        }
                     }
                 }
             } else {
@@ -340,16 +410,21 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
                     three = three && no_ascii && f0 == 0 && lead_lt_e0 == 0;
                 }
                 if (try_two && __all_sync(FULL_MASK, two)) {
-                    /* 16 characters: four bytes lead, continuation, lead,
-                     * continuation give two units, 110xxxxx 10yyyyyy -> x:y */
-                    const uint32_t wn = *reinterpret_cast<const uint32_t *>(row + BPT);
-                    const uint32_t r8 = (lm & 1u) ? 0u : 8u;   /* leads at odd bytes: windows one byte on */
+                    /* Every lane holds 16 characters, and in valid text in
+                     * the same phase (a chunk's last character ends where
+                     * the next chunk's first begins), so the warp's 512
+                     * characters start at r + 2 m, r being lane 0's first
+                     * lead: four bytes lead, continuation, lead,
+                     * continuation give two units, 110xxxxx 10yyyyyy -> x:y.
+                     * (Invalid text gives other units here, inside the
+                     * warp's 512, after its first error.) */
+                    const uint32_t r8 = __shfl_sync(FULL_MASK, (lm & 1u) ? 0u : 8u, 0);
 #pragma unroll
-                    for (int k = 0; k < WORDS; k++) {
-                        const uint32_t x = __funnelshift_r(w[k], k + 1 < WORDS ? w[k + 1] : wn, r8);
+                    for (int i = 0; i < WORDS; i++) {
+                        const uint32_t q = 32 * i + lane;
+                        const uint32_t x = __funnelshift_r(wsrc[q], wsrc[q + 1], r8);
                         const uint32_t u2 = ((x & 0x001F001Fu) << 6) | ((x >> 8) & 0x003F003Fu);
-                        out16[o + 2 * k] = (uint16_t)u2;
-                        out16[o + 2 * k + 1] = (uint16_t)(u2 >> 16);
+                        put_units2(out16, ow + 2 * q, u2);
                     }
                     lm = 0;
                 } else if (try_three && __all_sync(FULL_MASK, three)) {
@@ -426,22 +501,30 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
             if (tid == 0 && have_n) issue(tk, c_stage);
 
             /* write the tile's units [G0, G0 + cnt), clipped to the capacity,
-             * with aligned 16-byte stores assembled by funnel shifts */
+             * with aligned 16-byte stores: global vector i takes the staging
+             * bytes [16 i - shift, 16 i - shift + 16), from the staging
+             * granules i - 1 and i (whole 16-byte reads, consecutive across
+             * the lanes) */
             const uint64_t cnt = G0 >= cap ? 0 : (G0 + c_total > cap ? cap - G0 : c_total);
             const uint32_t shift = (uint32_t)((uintptr_t)(out + G0) & 15);
             uint8_t *gbase = reinterpret_cast<uint8_t *>(out + G0) - shift;
             const uint32_t lim = shift + 2 * (uint32_t)cnt;
             const uint32_t vf = shift ? 1u : 0u, vl = lim >> 4;   /* the whole vectors: [vf, vl) */
-            const uint32_t q = shift >> 2, r8 = 8 * (shift & 3);
             for (uint32_t i = vf + tid; i < vl; i += THREADS) {
-                const uint32_t j = 4 * i - q;
-                uint4 ov;
-                if (r8 == 0) {
-                    ov = make_uint4(outw[j], outw[j + 1], outw[j + 2], outw[j + 3]);
-                } else {   /* j >= 1: vf = 1 */
-                    const uint32_t w0 = outw[j - 1], w1 = outw[j], w2 = outw[j + 1], w3 = outw[j + 2], w4 = outw[j + 3];
-                    ov = make_uint4(__funnelshift_r(w0, w1, 32 - r8), __funnelshift_r(w1, w2, 32 - r8),
-                                    __funnelshift_r(w2, w3, 32 - r8), __funnelshift_r(w3, w4, 32 - r8));
+                const uint4 cur = outw4[i];
+                uint4 ov = cur;
+                if (shift) {   /* i >= 1: vf = 1 */
+                    const uint4 prv = outw4[i - 1];
+                    const uint32_t pw[8] = {prv.x, prv.y, prv.z, prv.w, cur.x, cur.y, cur.z, cur.w};
+                    switch (shift >> 1) {   /* even: units are 2 bytes */
+                    case 1: ov = window16<1>(pw); break;
+                    case 2: ov = window16<2>(pw); break;
+                    case 3: ov = window16<3>(pw); break;
+                    case 4: ov = window16<4>(pw); break;
+                    case 5: ov = window16<5>(pw); break;
+                    case 6: ov = window16<6>(pw); break;
+                    default: ov = window16<7>(pw); break;
+                    }
                 }
                 if (BE) {   /* UTF-16BE: each unit's two bytes the other way round (shift is even) */
                     ov.x = __byte_perm(ov.x, 0u, 0x2301);

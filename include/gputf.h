@@ -177,16 +177,21 @@ gputf_status gputf_utf8_length_from_utf16be(const uint16_t *in, size_t n_units, 
  * `d_in` holds the input, `d_out` out_cap units, `d_res` one gputf_result.
  * Pinned host memory makes the copies fastest.
  *
- * Inputs above 32 MiB are cut into chunks of about 32 MiB at the points
- * gputf_utf8_chunk_end / gputf_utf16_chunk_end give.  All host -> device
- * copies are issued at once.  Each chunk is transcoded on `stream` as soon as
- * its input has arrived, at the output written so far, with the capacity
- * left.  Its output is copied back while the next chunk is transcoded, so
- * the copies in both directions and the kernels overlap.  The first chunk
- * that reports an error or a full output ends the call.  `h_out`, `d_out` and
- * the result are those of the single call on the whole input.  Each call
- * creates two streams and some events and destroys them before it returns;
- * it allocates no memory.  It must not run inside a stream capture. */
+ * The input is cut into chunks at the points gputf_utf8_chunk_end /
+ * gputf_utf16_chunk_end give: about 4, 8 and 16 MiB, then 32 MiB each.  All
+ * host -> device copies are issued at once, and all chunks are launched at
+ * once on `stream`, each after its input has arrived.  Each chunk writes its
+ * output into d_out after the output of the chunks before it (the workspace
+ * carries that count from chunk to chunk on the device), within the capacity
+ * left.  As each chunk finishes, its output is copied back while later
+ * chunks run, so the copies in both directions and the kernels overlap.  The
+ * first chunk that reports an error or a full output gives the result.
+ * `h_out`, `d_out` and the result are those of the single call on the whole
+ * input (past the written units, d_out may hold more output, as it may after
+ * the single call).  The first call on a device creates two streams, some
+ * events and 1.5 KB of mapped pinned host memory for the chunks' results,
+ * kept for the process; calls on one device take turns.  The calls allocate
+ * no device memory.  They must not run inside a stream capture. */
 gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
                                       size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
@@ -196,9 +201,10 @@ gputf_status gputf_utf16_to_utf8_host(const uint16_t *h_in, size_t n_units, uint
                                       size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                       cudaStream_t stream);
 
-/* The same with the chunk size chosen by the caller, in input code units.
- * It is raised to 64, and to n / 63 when the input would need more than 64
- * chunks.  The default forms above pass 32 MiB of input. */
+/* The same with the chunk size chosen by the caller, in input code units
+ * (the first three chunks an eighth, a quarter and half of it).  It is raised
+ * to 64, and to n / 59 when n / chunk would reach 60 (at most 64 chunks).
+ * The default forms above pass 32 MiB of input. */
 gputf_status gputf_utf8_to_utf16_host_chunked(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,
                                               size_t out_cap, uint8_t *d_in, uint16_t *d_out, void *ws,
                                               size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,

@@ -1,7 +1,8 @@
 /*
  * C-ABI entry points of libgputf (declared in include/gputf.h): argument
  * checks, workspace sizing, device checks and kernel launches.  No entry
- * point allocates memory.
+ * point allocates device memory; the host forms keep a small per-device pool
+ * (streams, events, 1.5 KB of mapped pinned host memory) for the process.
  */
 #include <cstdint>
 #include <cstring>
@@ -96,7 +97,7 @@ cudaError_t launch_workspace_init(void *ws, uint64_t bytes, cudaStream_t s)
 namespace {
 gputf_status utf8_to_utf16_call(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap, void *ws,
                                 size_t ws_bytes, gputf_result *res, bool validate, bool big_endian,
-                                cudaStream_t stream)
+                                bool chained, cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_bytes, ws, ws_bytes, res, 1, &words);
@@ -107,12 +108,12 @@ gputf_status utf8_to_utf16_call(const uint8_t *in, size_t n_bytes, uint16_t *out
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf8_to_utf16(in, n_bytes, out, out_cap, ws, words,
                                                    reinterpret_cast<gputf::DevResult *>(res), sms, validate,
-                                                   big_endian, stream));
+                                                   big_endian, chained, stream));
 }
 
 gputf_status utf16_to_utf8_call(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap, void *ws,
                                 size_t ws_bytes, gputf_result *res, bool validate, bool big_endian,
-                                cudaStream_t stream)
+                                bool chained, cudaStream_t stream)
 {
     uint64_t words;
     gputf_status st = check_common(in, n_units, ws, ws_bytes, res, 2, &words);
@@ -123,7 +124,7 @@ gputf_status utf16_to_utf8_call(const uint16_t *in, size_t n_units, uint8_t *out
     if ((st = current_device(&sms)) != GPUTF_STATUS_OK) return st;
     return cuda_status(gputf::launch_utf16_to_utf8(in, n_units, out, out_cap, ws, words,
                                                    reinterpret_cast<gputf::DevResult *>(res), sms, validate,
-                                                   big_endian, stream));
+                                                   big_endian, chained, stream));
 }
 }  // namespace
 
@@ -150,25 +151,25 @@ gputf_status gputf_workspace_init(void *ws, size_t ws_bytes, cudaStream_t stream
 gputf_status gputf_utf8_to_utf16(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, false, stream);
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, false, false, stream);
 }
 
 gputf_status gputf_utf16_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                  void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, false, stream);
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, false, false, stream);
 }
 
 gputf_status gputf_utf8_to_utf16_unchecked(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap,
                                            void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, false, false, stream);
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, false, false, false, stream);
 }
 
 gputf_status gputf_utf16_to_utf8_unchecked(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap,
                                            void *ws, size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, false, false, stream);
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, false, false, false, stream);
 }
 
 gputf_status gputf_validate_utf8(const uint8_t *in, size_t n_bytes, void *ws, size_t ws_bytes,
@@ -234,13 +235,13 @@ gputf_status gputf_utf8_length_from_utf16(const uint16_t *in, size_t n_units, vo
 gputf_status gputf_utf16be_to_utf8(const uint16_t *in, size_t n_units, uint8_t *out, size_t out_cap, void *ws,
                                    size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, true, stream);
+    return utf16_to_utf8_call(in, n_units, out, out_cap, ws, ws_bytes, res, true, true, false, stream);
 }
 
 gputf_status gputf_utf8_to_utf16be(const uint8_t *in, size_t n_bytes, uint16_t *out, size_t out_cap, void *ws,
                                    size_t ws_bytes, gputf_result *res, cudaStream_t stream)
 {
-    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, true, stream);
+    return utf8_to_utf16_call(in, n_bytes, out, out_cap, ws, ws_bytes, res, true, true, false, stream);
 }
 
 gputf_status gputf_validate_utf16be(const uint16_t *in, size_t n_units, void *ws, size_t ws_bytes,
@@ -275,32 +276,75 @@ namespace {
 
 constexpr size_t HOST_MAX_CHUNKS = 64;
 
-/* Streams and events of one host-form call, released on every return path. */
-struct HostPipe {
+/* Per device, kept for the process: the host forms' two copy streams, the
+ * events that order their chunks, and mapped pinned host memory that the
+ * chunks' kernels write their results to (so the host reads a result without
+ * a device -> host copy, which would queue behind the output copies).  The
+ * lock makes host-form calls on one device take turns. */
+struct HostPool {
+    std::mutex m;
+    bool ready = false;
     cudaStream_t in = nullptr, out = nullptr;
-    cudaEvent_t start = nullptr, arrived[HOST_MAX_CHUNKS] = {};
-    size_t events = 0;
-    ~HostPipe()
+    cudaEvent_t start = nullptr, arrived[HOST_MAX_CHUNKS] = {}, finished[HOST_MAX_CHUNKS] = {};
+    gputf::DevResult *res_h = nullptr, *res_d = nullptr;
+};
+HostPool g_host_pools[MAX_DEVICES];
+
+cudaError_t host_pool_ready(HostPool &p)
+{
+    if (p.ready) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming)) != cudaSuccess)
+        return e;
+    for (size_t k = 0; k < HOST_MAX_CHUNKS; k++)
+        if ((e = cudaEventCreateWithFlags(&p.arrived[k], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p.finished[k], cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+    void *h = nullptr;
+    if ((e = cudaHostAlloc(&h, HOST_MAX_CHUNKS * sizeof(gputf::DevResult), cudaHostAllocMapped | cudaHostAllocPortable)) !=
+        cudaSuccess)
+        return e;
+    void *d = nullptr;
+    if ((e = cudaHostGetDevicePointer(&d, h, 0)) != cudaSuccess) {
+        cudaFreeHost(h);
+        return e;
+    }
+    p.res_h = static_cast<gputf::DevResult *>(h);
+    p.res_d = static_cast<gputf::DevResult *>(d);
+    p.ready = true;
+    return cudaSuccess;
+}
+
+/* Waits, on every return path, for the work a host-form call queued on the
+ * pool's streams and the caller's stream (it reads and writes the caller's
+ * buffers). */
+struct HostDrain {
+    cudaStream_t a, b, c;
+    ~HostDrain()
     {
-        if (in) cudaStreamSynchronize(in);
-        if (out) cudaStreamSynchronize(out);
-        for (size_t k = 0; k < events; k++) cudaEventDestroy(arrived[k]);
-        if (start) cudaEventDestroy(start);
-        if (in) cudaStreamDestroy(in);
-        if (out) cudaStreamDestroy(out);
+        cudaStreamSynchronize(a);
+        cudaStreamSynchronize(b);
+        cudaStreamSynchronize(c);
     }
 };
 
 /*
- * The host forms.  The input is cut into chunks of about `chunk` units at
- * points where the single call's results do not depend on what lies beyond
- * (gputf_*_chunk_end); all host -> device copies go out at once on one
- * stream; each chunk is transcoded on the caller's stream, as soon as its
- * input has arrived, into d_out at the output written so far, with the
- * capacity left; its `written` units go back to h_out on a third stream while
- * the next chunk is transcoded.  The first chunk that reports an error or a
- * full output ends the call, its position moved to the whole input's.  So
- * h_out, d_out and the result are the single call's.
+ * The host forms.  The input is cut into chunks at points where the single
+ * call's results do not depend on what lies beyond (gputf_*_chunk_end): the
+ * first ones chunk/8, chunk/4 and chunk/2 units long, so that output starts
+ * to come back early, then `chunk`.  All host -> device copies go out at once
+ * on one stream.  All chunks are launched at once on the caller's stream,
+ * each after its input has arrived, chained: it writes into d_out after the
+ * output units of the chunks before it, which the workspace header carries
+ * from chunk to chunk on the device, within the capacity left.  Each writes
+ * its result to the pool's mapped pinned memory; as each finishes, the host
+ * reads its `written` and copies those units back to h_out on a third stream
+ * while later chunks run.  The first chunk that reports an error or a full
+ * output ends the result (the chunks after it still run, writing beyond it in
+ * d_out, as the single call may), its position moved to the whole input's.
+ * So h_out, d_out and the result are the single call's.
  */
 template <typename TIn, typename TOut, typename Call, typename Cut>
 gputf_status host_form(const TIn *h_in, size_t n, TOut *h_out, size_t out_cap, TIn *d_in, TOut *d_out,
@@ -308,65 +352,74 @@ gputf_status host_form(const TIn *h_in, size_t n, TOut *h_out, size_t out_cap, T
                        size_t chunk, Call call, Cut cut)
 {
     if ((n > 0 && (h_in == nullptr || d_in == nullptr)) || h_res == nullptr || d_res == nullptr ||
-        (out_cap > 0 && (h_out == nullptr || d_out == nullptr)))
+        (out_cap > 0 && (h_out == nullptr || d_out == nullptr)) || ws == nullptr || !aligned(ws, 16))
         return GPUTF_STATUS_INVALID_ARGUMENT;
+    if (ws_bytes < gputf::HEADER_BYTES) return GPUTF_STATUS_WORKSPACE_TOO_SMALL;
     if (chunk < 64) chunk = 64;
-    if (n / chunk >= HOST_MAX_CHUNKS) chunk = n / (HOST_MAX_CHUNKS - 1);
-    HostPipe p;
-    cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventRecord(p.start, stream)) != cudaSuccess ||
+    if (n / chunk >= HOST_MAX_CHUNKS - 4) chunk = n / (HOST_MAX_CHUNKS - 5);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return GPUTF_STATUS_UNSUPPORTED_DEVICE;
+    HostPool &p = g_host_pools[dev];
+    std::lock_guard<std::mutex> lock(p.m);
+    if ((e = host_pool_ready(p)) != cudaSuccess) return cuda_status(e);
+    HostDrain drain{p.in, p.out, stream};
+    if ((e = cudaEventRecord(p.start, stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(p.in, p.start, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(p.out, p.start, 0)) != cudaSuccess)
         return cuda_status(e);
 
     /* chunk k is [a[k], a[k + 1]) */
     size_t a[HOST_MAX_CHUNKS + 1];
-    size_t chunks = 0;
+    size_t chunks = 0, step = chunk / 8 > 64 ? chunk / 8 : 64;
     a[0] = 0;
     while (a[chunks] < n || chunks == 0) {
-        const size_t next = chunks + 1 == HOST_MAX_CHUNKS ? n : cut(h_in, n, a[chunks] + chunk);
+        const size_t next = chunks + 1 == HOST_MAX_CHUNKS ? n : cut(h_in, n, a[chunks] + step);
         a[++chunks] = next;
+        step = 2 * step < chunk ? 2 * step : chunk;
         if (next >= n) break;
     }
     for (size_t k = 0; k < chunks; k++) {
-        if ((e = cudaEventCreateWithFlags(&p.arrived[k], cudaEventDisableTiming)) != cudaSuccess)
-            return cuda_status(e);
-        p.events = k + 1;
         const size_t len = a[k + 1] - a[k];
         if (len && (e = cudaMemcpyAsync(d_in + a[k], h_in + a[k], len * sizeof(TIn), cudaMemcpyHostToDevice,
                                         p.in)) != cudaSuccess)
             return cuda_status(e);
         if ((e = cudaEventRecord(p.arrived[k], p.in)) != cudaSuccess) return cuda_status(e);
     }
-
-    gputf_result total = {GPUTF_E_OK, 0, (uint64_t)n, 0};
-    uint64_t done = 0;   /* output units written by the chunks so far */
+    gputf::WsHeader *hdr = static_cast<gputf::WsHeader *>(ws);
+    if ((e = cudaMemsetAsync(&hdr->out_base, 0, sizeof hdr->out_base, stream)) != cudaSuccess)
+        return cuda_status(e);
     for (size_t k = 0; k < chunks; k++) {
         if ((e = cudaStreamWaitEvent(stream, p.arrived[k], 0)) != cudaSuccess) return cuda_status(e);
-        const gputf_status st = call(d_in + a[k], a[k + 1] - a[k], d_out + done, out_cap - done, ws, ws_bytes,
-                                     d_res, stream);
+        const gputf_status st = call(d_in + a[k], a[k + 1] - a[k], d_out, out_cap, ws, ws_bytes,
+                                     reinterpret_cast<gputf_result *>(p.res_d + k), stream);
         if (st != GPUTF_STATUS_OK) return st;
-        gputf_result r;
-        if ((e = cudaMemcpyAsync(&r, d_res, sizeof r, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-            return cuda_status(e);
-        const uint64_t w = r.written < out_cap - done ? r.written : out_cap - done;
+        if ((e = cudaEventRecord(p.finished[k], stream)) != cudaSuccess) return cuda_status(e);
+    }
+
+    gputf_result total = {GPUTF_E_OK, 0, (uint64_t)n, 0};
+    uint64_t done = 0;   /* output units of the chunks so far */
+    for (size_t k = 0; k < chunks; k++) {
+        if ((e = cudaEventSynchronize(p.finished[k])) != cudaSuccess) return cuda_status(e);
+        const volatile gputf::DevResult *vr = p.res_h + k;
+        const int32_t error = vr->error;
+        const uint64_t position = vr->position, written = vr->written;
+        const uint64_t w = written < out_cap - done ? written : out_cap - done;
         if (w && (e = cudaMemcpyAsync(h_out + done, d_out + done, w * sizeof(TOut), cudaMemcpyDeviceToHost,
                                       p.out)) != cudaSuccess)
             return cuda_status(e);
         done += w;
-        if (r.error != GPUTF_E_OK) {
-            total.error = r.error;
-            total.position = r.error == GPUTF_E_TIMEOUT ? 0 : a[k] + r.position;
-            total.written = r.error == GPUTF_E_TIMEOUT ? 0 : done;
+        if (error != GPUTF_E_OK) {
+            total.error = error;
+            total.position = error == GPUTF_E_TIMEOUT ? 0 : a[k] + position;
+            total.written = error == GPUTF_E_TIMEOUT ? 0 : done;
             break;
         }
         total.written = done;
     }
-    if ((e = cudaStreamSynchronize(p.out)) != cudaSuccess || (e = cudaStreamSynchronize(p.in)) != cudaSuccess)
+    if ((e = cudaStreamSynchronize(p.out)) != cudaSuccess || (e = cudaStreamSynchronize(stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(p.in)) != cudaSuccess)
         return cuda_status(e);
     *h_res = total;
     /* the device result as the single call leaves it */
@@ -386,8 +439,10 @@ gputf_status gputf_utf8_to_utf16_host_chunked(const uint8_t *h_in, size_t n_byte
                                               size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                               cudaStream_t stream, size_t chunk_bytes)
 {
+    auto call = [](const uint8_t *in, size_t n, uint16_t *out, size_t cap, void *w, size_t wb, gputf_result *r,
+                   cudaStream_t s) { return utf8_to_utf16_call(in, n, out, cap, w, wb, r, true, false, true, s); };
     return host_form(h_in, n_bytes, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res, h_res, stream, chunk_bytes,
-                     gputf_utf8_to_utf16, gputf_utf8_chunk_end);
+                     call, gputf_utf8_chunk_end);
 }
 
 gputf_status gputf_utf16_to_utf8_host_chunked(const uint16_t *h_in, size_t n_units, uint8_t *h_out,
@@ -395,8 +450,10 @@ gputf_status gputf_utf16_to_utf8_host_chunked(const uint16_t *h_in, size_t n_uni
                                               size_t ws_bytes, gputf_result *d_res, gputf_result *h_res,
                                               cudaStream_t stream, size_t chunk_units)
 {
+    auto call = [](const uint16_t *in, size_t n, uint8_t *out, size_t cap, void *w, size_t wb, gputf_result *r,
+                   cudaStream_t s) { return utf16_to_utf8_call(in, n, out, cap, w, wb, r, true, false, true, s); };
     return host_form(h_in, n_units, h_out, out_cap, d_in, d_out, ws, ws_bytes, d_res, h_res, stream, chunk_units,
-                     gputf_utf16_to_utf8, gputf_utf16_chunk_end);
+                     call, gputf_utf16_chunk_end);
 }
 
 gputf_status gputf_utf8_to_utf16_host(const uint8_t *h_in, size_t n_bytes, uint16_t *h_out,

@@ -43,7 +43,8 @@ struct WsHeader {
     unsigned long long accum;     /* sum of a length pass                      */
     unsigned int epoch;           /* current call epoch, 1 .. EPOCH_LIMIT-1    */
     unsigned int flags;           /* FLAG_TIMEOUT                              */
-    unsigned long long reserved[26];
+    unsigned long long out_base;  /* host forms: output units of the chunks before */
+    unsigned long long reserved[25];
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
 

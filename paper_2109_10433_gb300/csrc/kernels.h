@@ -22,10 +22,10 @@ uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n);
 
 cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 bool big_endian, cudaStream_t s);
+                                 bool big_endian, bool chained, cudaStream_t s);
 cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 bool big_endian, cudaStream_t s);
+                                 bool big_endian, bool chained, cudaStream_t s);
 cudaError_t launch_validate_utf8(const uint8_t *in, uint64_t n, void *ws, DevResult *res, int sms,
                                  cudaStream_t s);
 cudaError_t launch_validate_utf16(const uint16_t *in, uint64_t n, void *ws, DevResult *res, int sms,

@@ -204,7 +204,7 @@ template <int THREADS, int UPT, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, uint64_t tiles, DevResult *res)
+                     uint64_t status_words, uint64_t tiles, DevResult *res, bool chained)
 {
     using Lay = U16Layout<THREADS, UPT, STAGES>;
     constexpr uint64_t TILE = Lay::TILE;
@@ -229,6 +229,14 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     const uint16_t *base = in - head;
     const uint64_t endx = head + n;
     const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
+    /* a host form's chunks run chained: each writes its output after the
+     * units of the chunks before it, which the header holds (the previous
+     * chunk's last CTA moved it on) */
+    const uint64_t obase = chained ? ld_relaxed(&hdr->out_base) : 0;
+    if (chained) {
+        out += obase;
+        cap = cap > obase ? cap - obase : 0;
+    }
 
     /* thread 0: put tile t in flight into stage s */
     auto issue = [&](unsigned long long t, int s) {
@@ -575,6 +583,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         res->reserved = 0;
         res->position = pos;
         res->written = written;
+        if (chained) hdr->out_base = obase + written;
     }
     reset_workspace(hdr, status, status_words);
 }
@@ -737,7 +746,7 @@ uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
 
 template <bool VALIDATE, bool BE>
 static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap, void *ws,
-                            uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
+                            uint64_t status_words, DevResult *res, bool chained, int sms, cudaStream_t stream)
 {
     auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE, BE>;
     static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
@@ -753,19 +762,19 @@ static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
     kern<<<(unsigned)grid, U16_THREADS, U16Lay::SMEM, stream>>>(in, n, out, cap, hdr, status,
-                                                                 status_words, tiles, res);
+                                                                 status_words, tiles, res, chained);
     return cudaGetLastError();
 }
 
 cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 bool big_endian, cudaStream_t stream)
+                                 bool big_endian, bool chained, cudaStream_t stream)
 {
     if (big_endian)
-        return validate ? launch16<true, true>(in, n, out, cap, ws, status_words, res, sms, stream)
-                        : launch16<false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
-    return validate ? launch16<true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
-                    : launch16<false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
+        return validate ? launch16<true, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
+                        : launch16<false, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
+    return validate ? launch16<true, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
+                    : launch16<false, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

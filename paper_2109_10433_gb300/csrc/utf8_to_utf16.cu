@@ -182,7 +182,7 @@ template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE>
 __global__ void __launch_bounds__(THREADS)
 utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, uint64_t tiles, DevResult *res)
+                     uint64_t status_words, uint64_t tiles, DevResult *res, bool chained)
 {
     using Lay = U8Layout<THREADS, WORDS, STAGES>;
     constexpr int BPT = Lay::BPT;
@@ -206,6 +206,14 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     const uint8_t *base = in - head;
     const uint64_t endx = head + n;    /* extended index of the end position */
     const unsigned epoch = *(volatile unsigned *)&hdr->epoch;
+    /* a host form's chunks run chained: each writes its output after the
+     * units of the chunks before it, which the header holds (the previous
+     * chunk's last CTA moved it on) */
+    const uint64_t obase = chained ? ld_relaxed(&hdr->out_base) : 0;
+    if (chained) {
+        out += obase;
+        cap = cap > obase ? cap - obase : 0;
+    }
 
     /* thread 0: put tile t (already in stage s's ring entry) in flight into stage s */
     auto issue = [&](unsigned long long t, int s) {
@@ -632,6 +640,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
         res->reserved = 0;
         res->position = pos;
         res->written = written;
+        if (chained) hdr->out_base = obase + written;
     }
     reset_workspace(hdr, status, status_words);
 }
@@ -869,7 +878,7 @@ uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
 
 template <bool VALIDATE, bool BE>
 static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap, void *ws,
-                           uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
+                           uint64_t status_words, DevResult *res, bool chained, int sms, cudaStream_t stream)
 {
     auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE, BE>;
     static int per_sm = 0;
@@ -885,19 +894,19 @@ static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
     kern<<<(unsigned)grid, U8_THREADS, U8Lay::SMEM, stream>>>(in, n, out, cap, hdr, status, status_words,
-                                                              tiles, res);
+                                                              tiles, res, chained);
     return cudaGetLastError();
 }
 
 cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap,
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
-                                 bool big_endian, cudaStream_t stream)
+                                 bool big_endian, bool chained, cudaStream_t stream)
 {
     if (big_endian)
-        return validate ? launch8<true, true>(in, n, out, cap, ws, status_words, res, sms, stream)
-                        : launch8<false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
-    return validate ? launch8<true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
-                    : launch8<false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
+        return validate ? launch8<true, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
+                        : launch8<false, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
+    return validate ? launch8<true, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
+                    : launch8<false, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

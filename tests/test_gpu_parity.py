@@ -235,6 +235,21 @@ def test_host_buffer_forms(g, ws):
     assert np.array_equal(h_out.numpy()[:r.written], ref_out)
 
 
+def chunk_ends(chunk, n):
+    """Where the host forms cut an input of n units with chunk size `chunk`,
+    before each cut moves back to a character start: an eighth, a quarter
+    and half of `chunk` first (at least 64 units), then `chunk`."""
+    chunk = max(chunk, 64)
+    if n // chunk >= 60:   # at most 64 chunks
+        chunk = n // 59
+    ends, step, at = [], max(chunk // 8, 64), 0
+    while at < n:
+        at += step
+        ends.append(at)
+        step = min(2 * step, chunk)
+    return ends
+
+
 def test_host_forms_in_chunks(g, ws):
     """The host forms cut into many chunks: every result, the host output,
     the device output and the device result equal the single call's, with
@@ -247,7 +262,7 @@ def test_host_forms_in_chunks(g, ws):
         for variant in range(4):
             a = clean8.copy()
             if variant:   # a corrupted byte next to where a chunk ends
-                a[min(a.size - 1, int(rng.integers(1, 8)) * chunk + int(rng.integers(-3, 4)))] = 0xFF
+                a[min(a.size - 1, int(rng.choice(chunk_ends(chunk, a.size)[:8])) + int(rng.integers(-3, 4)))] = 0xFF
             for cap in (a.size, int(rng.integers(1, a.size))):
                 h_in = torch.from_numpy(a).pin_memory()
                 h_out = torch.full((cap,), GUARD * 257, dtype=torch.int16).pin_memory()
@@ -262,7 +277,8 @@ def test_host_forms_in_chunks(g, ws):
         for variant in range(4):
             u = clean16.copy()
             if variant:   # a lone surrogate next to where a chunk ends
-                u[min(u.size - 1, int(rng.integers(1, 8)) * chunk + int(rng.integers(-2, 3)))] = 0xD800 + variant
+                u[min(u.size - 1, int(rng.choice(chunk_ends(chunk, u.size)[:8])) + int(rng.integers(-2, 3)))] = \
+                    0xD800 + variant
             for cap in (3 * u.size, int(rng.integers(1, 3 * u.size))):
                 h_in = torch.from_numpy(u.view(np.int16)).pin_memory()
                 h_out = torch.full((cap,), GUARD, dtype=torch.uint8).pin_memory()

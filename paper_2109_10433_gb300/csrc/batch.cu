@@ -252,11 +252,14 @@ __device__ void block_seg_scan(bool f, uint64_t v, BatchShared &sm, bool *ef, ui
 }
 
 /* Segmented look-back: the sum carried into tile t from the string it
- * begins inside.  Warp 0 walks back 32 tiles at a time, waiting (bounded)
- * for each status word, and stops at the nearest tile that published an
- * inclusive prefix or holds a string start (usually the tile just before);
- * the other warps only wait for the result.  Called by all threads; returns
- * the value to every thread. */
+ * begins inside.  Warp 0 reads the status words of the 32 tiles before t
+ * (lane L: tile t - 1 - L) and stops at the nearest tile that published an
+ * inclusive prefix or holds a string start (usually the tile just before),
+ * once every tile nearer than that one has published its aggregate; tiles
+ * beyond the stop are not waited for.  With no stop among 32 published
+ * words it moves 32 tiles back.  The polls are bounded; the other warps
+ * only wait for the result.  Called by all threads; returns the value to
+ * every thread. */
 template <int THREADS>
 __device__ uint64_t block_seg_look_back(unsigned long long *status, long long tile, unsigned epoch,
                                         unsigned *flags, BatchShared &sm)
@@ -265,34 +268,41 @@ __device__ uint64_t block_seg_look_back(unsigned long long *status, long long ti
     if (threadIdx.x < 32) {
         uint64_t carry = 0;
         long long end = tile - 1;
+        int spins = 0;
         while (end >= 0) {
             const long long idx = end - lane;
-            bool stop = true;
+            unsigned ns = 32;
             uint64_t value = 0;
-            if (idx >= 0) {
-                int spins = 0;
-                unsigned ns = 32;
-                while (true) {
+            unsigned pmask;
+            bool timed_out = false;
+            for (;;) {
+                bool ok = true, stop = true;   /* before tile 0: the start, adding nothing */
+                value = 0;
+                if (idx >= 0) {
                     const uint64_t w = ld_acquire(status + idx);
                     const uint64_t fl = (w >> 40) & 3;
-                    if ((unsigned)(w >> 43) == (epoch & SEG_EPOCH_MASK) && fl != 0) {
-                        stop = fl == ST_PREFIX || ((w >> 42) & 1);
-                        value = w & VALUE_MASK;
-                        break;
-                    }
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(flags, FLAG_TIMEOUT);
-                        stop = true;
-                        value = 0;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
+                    ok = (unsigned)(w >> 43) == (epoch & SEG_EPOCH_MASK) && fl != 0;
+                    stop = ok && (fl == ST_PREFIX || ((w >> 42) & 1));
+                    value = w & VALUE_MASK;
                 }
+                pmask = __ballot_sync(FULL_MASK, stop);
+                const unsigned umask = __ballot_sync(FULL_MASK, !ok);
+                const unsigned nearer = pmask ? (pmask & (0u - pmask)) - 1u : FULL_MASK;   /* lanes before the stop */
+                if ((umask & nearer) == 0) break;
+                if (++spins > SPIN_LIMIT) {
+                    timed_out = true;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
             }
-            const unsigned pmask = __ballot_sync(FULL_MASK, stop);
+            if (timed_out) {
+                if (lane == 0) atomicOr(flags, FLAG_TIMEOUT);
+                carry = 0;
+                break;
+            }
             const int st = pmask ? __ffs(pmask) - 1 : 31;
-            uint64_t v = lane <= st ? value : 0;
+            uint64_t v = (lane <= st && idx >= 0) ? value : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
             carry += v;
@@ -303,6 +313,38 @@ __device__ uint64_t block_seg_look_back(unsigned long long *status, long long ti
     }
     __syncthreads();
     return sm.lb_sum[0];
+}
+
+/* Position x relative to a thread's first unit c0, clamped to [-8, lim]:
+ * exact wherever the per-unit loops compare it (string starts within 8
+ * units before the chunk, ends up to lim). */
+__device__ __forceinline__ int rel_pos(uint64_t x, uint64_t c0, int lim)
+{
+    const long long r = (long long)(x - c0);
+    return r < -8 ? -8 : (r > lim ? lim : (int)r);
+}
+
+/* Stages input elements [x0 - halo, x0 + count - halo) of a direction (bytes
+ * `esize` each; zeros outside [0, units)): whole 16-byte vectors when the
+ * span lies inside the input and starts 16-byte aligned, else element by
+ * element. */
+template <typename T, int THREADS>
+__device__ __forceinline__ void stage_fill(T *stage, const T *in, uint64_t x0, uint64_t units, int halo, int count)
+{
+    const int tid = threadIdx.x;
+    const bool whole = x0 >= (uint64_t)halo && x0 - halo + count <= units &&
+                       ((uintptr_t)(in + (x0 - halo)) & 15) == 0 && (count * sizeof(T)) % 16 == 0;
+    if (whole) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(in + (x0 - halo));
+        uint4 *dst = reinterpret_cast<uint4 *>(stage);
+        const int nv = count * (int)sizeof(T) / 16;
+        for (int i = tid; i < nv; i += THREADS) dst[i] = src[i];
+    } else {
+        for (int i = tid; i < count; i += THREADS) {
+            const long long x = (long long)x0 + i - halo;
+            stage[i] = (x >= 0 && (uint64_t)x < units) ? in[x] : T(0);
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------
@@ -407,10 +449,7 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
     const uint64_t x1 = x0 + TILE < d.units ? x0 + TILE : d.units;
 
     if (tid < 32) find_strings(d, sm, x0, t + 1 == d.tiles ? ~0ull : x1);
-    for (int i = tid; i < (int)TILE + 2 * HALO; i += THREADS) {
-        const long long x = (long long)x0 + i - HALO;
-        stage[i] = (x >= 0 && (uint64_t)x < d.units) ? in[x] : 0;
-    }
+    stage_fill<uint16_t, THREADS>(stage, in, x0, d.units, HALO, (int)TILE + 2 * HALO);
     __syncthreads();
 
     /* this thread's units [c0, c1) and the string holding c0 */
@@ -429,34 +468,42 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
         s = sm.s_first + lo;
     }
 #define U16AT(x) ((uint32_t)stage[(x) - x0 + HALO])
-    /* phase A: bytes per unit, starts, errors */
+    /* phase A: bytes per unit, starts, errors.  Positions are taken
+     * relative to c0 (j = i - c0) and the units slide through prev, u and
+     * next, one stage read each. */
+    const int base = tid * UPT + HALO;   /* stage index of c0 */
+    const int nloc = (int)(c1 - c0);
     bool f = false;
     uint64_t v = 0;
-    if (c0 < c1) {
+    if (nloc > 0) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
-        uint64_t err_s = NONE, err_p = NONE;
-        for (uint64_t i = c0; i < c1; i++) {
-            while (i >= en) {
+        int stl = rel_pos(st, c0, UPT + 8), enl = rel_pos(en, c0, UPT + 8);
+        uint64_t err_s = NONE;
+        uint32_t prev = stl < 0 ? (uint32_t)stage[base - 1] : 0u, u = stage[base];
+        for (int j = 0; j < nloc; j++) {
+            while (j >= enl) {
                 ss++;
                 st = en;
+                stl = enl;
                 en = off_at(d, sm, ss + 1);
+                enl = rel_pos(en, c0, UPT + 8);
             }
-            if (i == st) {
+            if (j == stl) {
                 f = true;
                 v = 0;
+                prev = 0;
             }
-            const uint32_t u = U16AT(i);
-            const uint32_t prev = i > st ? U16AT(i - 1) : 0u;
-            const uint32_t next = i + 1 < en ? U16AT(i + 1) : 0u;
+            const uint32_t nx = stage[base + j + 1];
+            const uint32_t next = j + 1 < enl ? nx : 0u;
             v += bytes16(u, prev, next);
             const bool bad = (is_hi16(u) && !is_lo16(next)) || (is_lo16(u) && !is_hi16(prev));
             if (bad && err_s != ss) {
-                record_string_error(d.errw, ss, epoch, i - st);
+                record_string_error(d.errw, ss, epoch, c0 + j - st);
                 err_s = ss;
-                err_p = i;
             }
+            prev = u;
+            u = nx;
         }
-        (void)err_p;
     }
     /* The look-back also orders the error words: a string's result is read
      * only after every tile from its first on has published, so it runs
@@ -475,26 +522,32 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
     __threadfence();
 
     /* phase B: bytes out, results of strings ending here */
-    if (c0 < c1) {
+    if (nloc > 0) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        int stl = rel_pos(st, c0, UPT + 8), enl = rel_pos(en, c0, UPT + 8);
         uint64_t g = ef ? ev : carry + ev;   /* output position within the string */
         uint64_t ob = wr ? d.out_off[ss] : 0, oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
-        for (uint64_t i = c0; i < c1; i++) {
-            while (i >= en) {
+        uint32_t prev = stl < 0 ? (uint32_t)stage[base - 1] : 0u, u = stage[base];
+        for (int j = 0; j < nloc; j++) {
+            while (j >= enl) {
                 ss++;
                 st = en;
+                stl = enl;
                 en = off_at(d, sm, ss + 1);
+                enl = rel_pos(en, c0, UPT + 8);
                 ob = wr ? d.out_off[ss] : 0;
                 oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
             }
-            if (i == st) g = 0;
-            const uint32_t u = U16AT(i);
-            const uint32_t prev = i > st ? U16AT(i - 1) : 0u;
-            const uint32_t next = i + 1 < en ? U16AT(i + 1) : 0u;
+            if (j == stl) {
+                g = 0;
+                prev = 0;
+            }
+            const uint32_t nx = stage[base + j + 1];
+            const uint32_t next = j + 1 < enl ? nx : 0u;
             const uint32_t l = bytes16(u, prev, next);
             if (wr && l && g + l <= oc) put_bytes16(out + ob + g, u, next, l);
             g += l;
-            if (i + 1 == en) {   /* the string's last unit: its result */
+            if (j + 1 == enl) {   /* the string's last unit: its result */
                 const uint64_t e = string_error(d.errw, ss, epoch);
                 if (e == NONE && g <= oc) {
                     d.res[ss].error = GPUTF_E_OK;
@@ -505,6 +558,8 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
                     finish_string16<TILE>(d, epoch, ss, e, g);
                 }
             }
+            prev = u;
+            u = nx;
         }
     }
 #undef U16AT
@@ -596,10 +651,7 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
     const uint64_t x1 = x0 + TILE < d.units ? x0 + TILE : d.units;
 
     if (tid < 32) find_strings(d, sm, x0, t + 1 == d.tiles ? ~0ull : x1);
-    for (int i = tid; i < (int)TILE + 2 * HALO; i += THREADS) {
-        const long long x = (long long)x0 + i - HALO;
-        stage[i] = (x >= 0 && (uint64_t)x < d.units) ? in[x] : 0;
-    }
+    stage_fill<uint8_t, THREADS>(stage, in, x0, d.units, HALO, (int)TILE + 2 * HALO);
     __syncthreads();
 
     const uint64_t c0 = x0 + (uint64_t)tid * BPT;
@@ -628,32 +680,38 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
             fl |= ((((nz >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
         }
     }
-    /* phase A: units per byte, starts, first flagged byte per string */
+    /* phase A: units per byte, starts, first flagged byte per string, with
+     * positions relative to c0 (j = i - c0) */
+    const int base = tid * BPT + HALO;   /* stage index of c0 */
+    const int nloc = (int)(c1 - c0);
     bool f = false;
     uint64_t v = 0;
-    if (c0 < c1) {
+    if (nloc > 0) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        int stl = rel_pos(st, c0, BPT + 8), enl = rel_pos(en, c0, BPT + 8);
         uint64_t flagged = NONE;
-        for (uint64_t i = c0; i < c1; i++) {
-            while (i >= en) {
+        for (int j = 0; j < nloc; j++) {
+            while (j >= enl) {
                 ss++;
                 st = en;
+                stl = enl;
                 en = off_at(d, sm, ss + 1);
+                enl = rel_pos(en, c0, BPT + 8);
             }
-            if (i == st) {
+            if (j == stl) {
                 f = true;
                 v = 0;
             }
-            const uint32_t b = stage[SIDX(i)];
+            const uint32_t b = stage[base + j];
             v += len16_of(b);
             /* the flag sees the string's own bytes before i (the halo holds
              * the 7 before the tile) and zeros before the string's start */
-            const bool fi = i - st < 3 ? flag_at(stage, SIDX(i), SIDX(st), SIDX(en)) : ((fl >> (i - c0)) & 1u) != 0;
+            const bool fi = j - stl < 3 ? flag_at(stage, base + j, base + stl, base + enl) : ((fl >> j) & 1u) != 0;
             if (flagged != ss && fi) {
-                record_string_error(d.errw, ss, epoch, i - st);
+                record_string_error(d.errw, ss, epoch, c0 + j - st);
                 flagged = ss;
             }
-            if (i + 1 == en && flagged != ss && flag_at(stage, SIDX(en), SIDX(st), SIDX(en))) {   /* cut short at its end */
+            if (j + 1 == enl && flagged != ss && flag_at(stage, base + enl, base + stl, base + enl)) {   /* cut short at its end */
                 record_string_error(d.errw, ss, epoch, en - st);
                 flagged = ss;
             }
@@ -675,26 +733,32 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
     if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
     __threadfence();
 
-    /* phase B: units out at each lead, results of strings ending here */
-    if (c0 < c1) {
+    /* phase B: units out at each lead, results of strings ending here; a
+     * lead's four bytes come from two stage words, those past the string's
+     * end cleared */
+    if (nloc > 0) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
+        int stl = rel_pos(st, c0, BPT + 8), enl = rel_pos(en, c0, BPT + 8);
         uint64_t g = ef ? ev : carry + ev;
         uint64_t ob = wr ? d.out_off[ss] : 0, oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
-        for (uint64_t i = c0; i < c1; i++) {
-            while (i >= en) {
+        for (int j = 0; j < nloc; j++) {
+            while (j >= enl) {
                 ss++;
                 st = en;
+                stl = enl;
                 en = off_at(d, sm, ss + 1);
+                enl = rel_pos(en, c0, BPT + 8);
                 ob = wr ? d.out_off[ss] : 0;
                 oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
             }
-            if (i == st) g = 0;
-            const uint32_t b = stage[SIDX(i)];
+            if (j == stl) g = 0;
+            const uint32_t b = stage[base + j];
             if (wr && (b & 0xC0) != 0x80) {
-                uint32_t q = b;
-#pragma unroll
-                for (int k = 1; k < 4; k++)
-                    q |= (i + k < en ? (uint32_t)stage[SIDX(i + k)] : 0u) << (8 * k);
+                const int p = base + j;
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(stage + (p & ~3));
+                uint32_t q = __funnelshift_r(wp[0], wp[1], 8 * (p & 3));
+                const int rem = enl - j;   /* bytes of the string from this lead on, at least 1 */
+                if (rem < 4) q &= (1u << (8 * rem)) - 1u;
                 const uint32_t b0 = q & 0xFF;
                 const uint32_t two = ((b0 & 0x1F) << 6) | ((q >> 8) & 0x3F);
                 const uint32_t three = ((b0 & 0x0F) << 12) | ((q >> 2) & 0x0FC0) | ((q >> 16) & 0x3F);
@@ -712,7 +776,7 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                 }
                 g += l;
             }
-            if (i + 1 == en) {
+            if (j + 1 == enl) {
                 const uint64_t e = string_error(d.errw, ss, epoch);
                 if (e == NONE && g <= oc) {
                     d.res[ss].error = GPUTF_E_OK;

@@ -324,6 +324,12 @@ __device__ __forceinline__ int rel_pos(uint64_t x, uint64_t c0, int lim)
     return r < -8 ? -8 : (r > lim ? lim : (int)r);
 }
 
+/* Bits [a, b) of a word, 0 <= a < b <= 32. */
+__device__ __forceinline__ uint32_t bit_range(int a, int b)
+{
+    return (b >= 32 ? 0u : (1u << b)) - (1u << a);
+}
+
 /* Stages input elements [x0 - halo, x0 + count - halo) of a direction (bytes
  * `esize` each; zeros outside [0, units)): whole 16-byte vectors when the
  * span lies inside the input and starts 16-byte aligned, else element by
@@ -667,21 +673,27 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
         s = sm.s_first + lo;
     }
 #define SIDX(x) ((long long)((x) - x0) + HALO)
-    /* error flags of the chunk's bytes, each checked against the three
-     * bytes before it whatever string they belong to (bit j: byte c0 + j);
-     * exact for every byte at least three past its string's start */
-    uint32_t fl = 0;
+    /* per byte of the chunk (bit j: byte c0 + j): error flags, each checked
+     * against the three bytes before it whatever string they belong to
+     * (exact for every byte at least three past its string's start);
+     * leads (not 10xxxxxx: one unit each); 4-byte leads (one more) */
+    uint32_t fl = 0, lb = 0, fb = 0;
     if (c0 < c1) {
         const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage + SIDX(c0));
         gputf_u8state u8s = gputf_u8state_of(sw[-1]);
 #pragma unroll
         for (int k = 0; k < BPT / 4; k++) {
-            const uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors_step(&u8s, sw[k]));
+            const uint32_t x = sw[k];
+            const uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors_step(&u8s, x));
             fl |= ((((nz >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+            const uint32_t ld = ~(x & ~(x << 1)) & 0x80808080u;
+            const uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
+            lb |= ((((ld >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+            fb |= ((((f4 >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
         }
     }
-    /* phase A: units per byte, starts, first flagged byte per string, with
-     * positions relative to c0 (j = i - c0) */
+    /* phase A, one string piece of the chunk at a time (positions j
+     * relative to c0): units, starts, the first flagged byte per string */
     const int base = tid * BPT + HALO;   /* stage index of c0 */
     const int nloc = (int)(c1 - c0);
     bool f = false;
@@ -690,7 +702,8 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
         int stl = rel_pos(st, c0, BPT + 8), enl = rel_pos(en, c0, BPT + 8);
         uint64_t flagged = NONE;
-        for (int j = 0; j < nloc; j++) {
+        int j = 0;
+        while (j < nloc) {
             while (j >= enl) {
                 ss++;
                 st = en;
@@ -698,23 +711,30 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                 en = off_at(d, sm, ss + 1);
                 enl = rel_pos(en, c0, BPT + 8);
             }
+            const int pe = enl < nloc ? enl : nloc;   /* the piece [j, pe) */
+            const uint32_t pm = bit_range(j, pe);
             if (j == stl) {
                 f = true;
                 v = 0;
             }
-            const uint32_t b = stage[base + j];
-            v += len16_of(b);
-            /* the flag sees the string's own bytes before i (the halo holds
-             * the 7 before the tile) and zeros before the string's start */
-            const bool fi = j - stl < 3 ? flag_at(stage, base + j, base + stl, base + enl) : ((fl >> j) & 1u) != 0;
-            if (flagged != ss && fi) {
-                record_string_error(d.errw, ss, epoch, c0 + j - st);
+            v += __popc(lb & pm) + __popc(fb & pm);
+            /* the string's first three bytes see only its own bytes before
+             * them (zeros before its start): their flags are taken exactly */
+            uint32_t fm = fl & pm;
+            const int e3 = stl + 3 < pe ? stl + 3 : pe;
+            for (int k = stl > j ? stl : j; k < e3; k++) {
+                if (flag_at(stage, base + k, base + stl, base + enl)) fm |= 1u << k;
+                else fm &= ~(1u << k);
+            }
+            if (flagged != ss && fm) {
+                record_string_error(d.errw, ss, epoch, c0 + (__ffs(fm) - 1) - st);
                 flagged = ss;
             }
-            if (j + 1 == enl && flagged != ss && flag_at(stage, base + enl, base + stl, base + enl)) {   /* cut short at its end */
+            if (pe == enl && flagged != ss && flag_at(stage, base + enl, base + stl, base + enl)) {   /* cut short at its end */
                 record_string_error(d.errw, ss, epoch, en - st);
                 flagged = ss;
             }
+            j = pe;
         }
     }
     /* The look-back also orders the error words: a string's result is read
@@ -733,15 +753,16 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
     if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
     __threadfence();
 
-    /* phase B: units out at each lead, results of strings ending here; a
-     * lead's four bytes come from two stage words, those past the string's
-     * end cleared */
+    /* phase B, one string piece at a time: units out at each lead (its
+     * four bytes from two stage words, those past the string's end
+     * cleared), results of strings ending here */
     if (nloc > 0) {
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
         int stl = rel_pos(st, c0, BPT + 8), enl = rel_pos(en, c0, BPT + 8);
         uint64_t g = ef ? ev : carry + ev;
         uint64_t ob = wr ? d.out_off[ss] : 0, oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
-        for (int j = 0; j < nloc; j++) {
+        int j = 0;
+        while (j < nloc) {
             while (j >= enl) {
                 ss++;
                 st = en;
@@ -752,31 +773,36 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                 oc = wr ? d.out_off[ss + 1] - ob : ~0ull;
             }
             if (j == stl) g = 0;
-            const uint32_t b = stage[base + j];
-            if (wr && (b & 0xC0) != 0x80) {
-                const int p = base + j;
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(stage + (p & ~3));
-                uint32_t q = __funnelshift_r(wp[0], wp[1], 8 * (p & 3));
-                const int rem = enl - j;   /* bytes of the string from this lead on, at least 1 */
-                if (rem < 4) q &= (1u << (8 * rem)) - 1u;
-                const uint32_t b0 = q & 0xFF;
-                const uint32_t two = ((b0 & 0x1F) << 6) | ((q >> 8) & 0x3F);
-                const uint32_t three = ((b0 & 0x0F) << 12) | ((q >> 2) & 0x0FC0) | ((q >> 16) & 0x3F);
-                const uint32_t four = ((b0 & 0x07) << 18) | ((q << 4) & 0x3F000) | ((q >> 10) & 0x0FC0) |
-                                      ((q >> 24) & 0x3F);
-                const uint32_t x = four - 0x10000;
-                const uint32_t l = len16_of(b);
-                if (g + l <= oc) {
-                    if (l == 2) {
-                        out[ob + g] = (uint16_t)(0xD800 | ((x >> 10) & 0x3FF));
-                        out[ob + g + 1] = (uint16_t)(0xDC00 | (x & 0x3FF));
-                    } else {
-                        out[ob + g] = (uint16_t)(b0 < 0x80 ? b0 : (b0 < 0xE0 ? two : three));
+            const int pe = enl < nloc ? enl : nloc;
+            if (wr) {
+                uint32_t lm = lb & bit_range(j, pe);
+                while (lm) {
+                    const int k = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const int p = base + k;
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(stage + (p & ~3));
+                    uint32_t q = __funnelshift_r(wp[0], wp[1], 8 * (p & 3));
+                    const int rem = enl - k;   /* bytes of the string from this lead on, at least 1 */
+                    if (rem < 4) q &= (1u << (8 * rem)) - 1u;
+                    const uint32_t b0 = q & 0xFF;
+                    const uint32_t two = ((b0 & 0x1F) << 6) | ((q >> 8) & 0x3F);
+                    const uint32_t three = ((b0 & 0x0F) << 12) | ((q >> 2) & 0x0FC0) | ((q >> 16) & 0x3F);
+                    const uint32_t four = ((b0 & 0x07) << 18) | ((q << 4) & 0x3F000) | ((q >> 10) & 0x0FC0) |
+                                          ((q >> 24) & 0x3F);
+                    const uint32_t x = four - 0x10000;
+                    const uint32_t l = len16_of(b0);
+                    if (g + l <= oc) {
+                        if (l == 2) {
+                            out[ob + g] = (uint16_t)(0xD800 | ((x >> 10) & 0x3FF));
+                            out[ob + g + 1] = (uint16_t)(0xDC00 | (x & 0x3FF));
+                        } else {
+                            out[ob + g] = (uint16_t)(b0 < 0x80 ? b0 : (b0 < 0xE0 ? two : three));
+                        }
                     }
+                    g += l;
                 }
-                g += l;
             }
-            if (j + 1 == enl) {
+            if (pe == enl) {   /* the string's last byte is here: its result */
                 const uint64_t e = string_error(d.errw, ss, epoch);
                 if (e == NONE && g <= oc) {
                     d.res[ss].error = GPUTF_E_OK;
@@ -787,6 +813,7 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                     finish_string8<TILE>(d, epoch, ss, e, g);
                 }
             }
+            j = pe;
         }
     }
 #undef SIDX

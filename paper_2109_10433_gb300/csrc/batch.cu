@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "utf16_scheme.h"
 #include "kernels.h"
 
 namespace gputf {
@@ -324,6 +325,12 @@ __device__ __forceinline__ int rel_pos(uint64_t x, uint64_t c0, int lim)
     return r < -8 ? -8 : (r > lim ? lim : (int)r);
 }
 
+/* Bit 7 of each byte of m gathered into bits 0-3 (byte k -> bit k). */
+__device__ __forceinline__ uint32_t gather_bit7(uint32_t m)
+{
+    return (((m >> 7) & 0x01010101u) * 0x01020408u) >> 24;
+}
+
 /* Bits [a, b) of a word, 0 <= a < b <= 32. */
 __device__ __forceinline__ uint32_t bit_range(int a, int b)
 {
@@ -474,19 +481,48 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
         s = sm.s_first + lo;
     }
 #define U16AT(x) ((uint32_t)stage[(x) - x0 + HALO])
-    /* phase A: bytes per unit, starts, errors.  Positions are taken
-     * relative to c0 (j = i - c0) and the units slide through prev, u and
-     * next, one stage read each. */
+    /* phase A, one string piece of the chunk at a time (positions j
+     * relative to c0): bytes, starts, errors, from bit masks over the
+     * chunk's units.  A piece's bytes are Table 2's closed form (a surrogate
+     * counts 2, so a pair inside the piece gives its 4), corrected where a
+     * pair crosses the chunk's edge: its low half writes nothing here, or
+     * its high half writes all 4.  A unit breaks the pairing rule when it is
+     * high and the next is not low, or low and the one before is not high,
+     * with nothing before a string's first unit or after its last. */
     const int base = tid * UPT + HALO;   /* stage index of c0 */
     const int nloc = (int)(c1 - c0);
     bool f = false;
     uint64_t v = 0;
     if (nloc > 0) {
+        uint32_t w[UPT / 2];
+#pragma unroll
+        for (int q = 0; q < UPT / 8; q++) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(stage + base + 8 * q);
+            w[4 * q + 0] = x.x;
+            w[4 * q + 1] = x.y;
+            w[4 * q + 2] = x.z;
+            w[4 * q + 3] = x.w;
+        }
+        uint32_t m80 = 0, m3 = 0, hi = 0, lo = 0;   /* bit k: unit c0 + k */
+#pragma unroll
+        for (int g4 = 0; g4 < UPT / 4; g4++) {
+            const uint32_t H = gputf_bperm(w[2 * g4], w[2 * g4 + 1], 0x7531);   /* high bytes */
+            const uint32_t L = gputf_bperm(w[2 * g4], w[2 * g4 + 1], 0x6420);   /* low bytes */
+            const uint32_t ge80 = ~(gputf_zero_bytes(H) & ~L) & 0x80808080u;
+            const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;
+            const uint32_t sur = gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
+            const uint32_t t = H << 5;   /* bit 2 of the high byte: a low surrogate */
+            m80 |= gather_bit7(ge80) << (4 * g4);
+            m3 |= gather_bit7(ge08 & ~sur) << (4 * g4);
+            hi |= gather_bit7(sur & ~t) << (4 * g4);
+            lo |= gather_bit7(sur & t) << (4 * g4);
+        }
+        const bool pu_hi = is_hi16(stage[base - 1]), nu_lo = is_lo16(stage[base + nloc]);
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
         int stl = rel_pos(st, c0, UPT + 8), enl = rel_pos(en, c0, UPT + 8);
         uint64_t err_s = NONE;
-        uint32_t prev = stl < 0 ? (uint32_t)stage[base - 1] : 0u, u = stage[base];
-        for (int j = 0; j < nloc; j++) {
+        int j = 0;
+        while (j < nloc) {
             while (j >= enl) {
                 ss++;
                 st = en;
@@ -494,21 +530,27 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
                 en = off_at(d, sm, ss + 1);
                 enl = rel_pos(en, c0, UPT + 8);
             }
+            const int pe = enl < nloc ? enl : nloc;   /* the piece [j, pe) */
+            const uint32_t pm = bit_range(j, pe), fb = 1u << j, lb = 1u << (pe - 1);
             if (j == stl) {
                 f = true;
                 v = 0;
-                prev = 0;
             }
-            const uint32_t nx = stage[base + j + 1];
-            const uint32_t next = j + 1 < enl ? nx : 0u;
-            v += bytes16(u, prev, next);
-            const bool bad = (is_hi16(u) && !is_lo16(next)) || (is_lo16(u) && !is_hi16(prev));
+            /* a piece starts at its string's start or at the chunk's start,
+             * and ends at its string's end or at the chunk's end */
+            const bool ph = j != stl && pu_hi;                    /* the unit before the piece is high */
+            const bool nl = pe != enl && nu_lo;                   /* the unit after the piece is low */
+            v += __popc(pm) + __popc(m80 & pm) + __popc(m3 & pm);
+            if ((lo & fb) && ph) v -= 2;
+            if ((hi & lb) && nl) v += 2;
+            const uint32_t prevhi = ((hi << 1) & ~fb) | (ph ? fb : 0u);
+            const uint32_t nextlo = ((lo >> 1) & ~lb) | (nl ? lb : 0u);
+            const uint32_t bad = ((hi & ~nextlo) | (lo & ~prevhi)) & pm;
             if (bad && err_s != ss) {
-                record_string_error(d.errw, ss, epoch, c0 + j - st);
+                record_string_error(d.errw, ss, epoch, c0 + (__ffs(bad) - 1) - st);
                 err_s = ss;
             }
-            prev = u;
-            u = nx;
+            j = pe;
         }
     }
     /* The look-back also orders the error words: a string's result is read

@@ -200,11 +200,14 @@ struct U16Layout {
  * mbarriers.  Tiles at the ends of the buffer (halo outside the input) are
  * filled by the threads with guarded loads instead.
  */
-template <int THREADS, int UPT, int STAGES, bool VALIDATE, bool BE>
-__global__ void __launch_bounds__(THREADS)
+template <int THREADS, int UPT, int STAGES, bool VALIDATE, bool BE, bool CHAINED>
+/* CHAINED (the host forms' chunks) is a separate instance, held to 5 CTAs
+ * per SM: as a runtime flag, its output base cost the single calls 16
+ * registers and a CTA per SM */
+__global__ void __launch_bounds__(THREADS, CHAINED ? 5 : 0)
 utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, uint64_t tiles, DevResult *res, bool chained)
+                     uint64_t status_words, uint64_t tiles, DevResult *res)
 {
     using Lay = U16Layout<THREADS, UPT, STAGES>;
     constexpr uint64_t TILE = Lay::TILE;
@@ -232,8 +235,8 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
     /* a host form's chunks run chained: each writes its output after the
      * units of the chunks before it, which the header holds (the previous
      * chunk's last CTA moved it on) */
-    const uint64_t obase = chained ? ld_relaxed(&hdr->out_base) : 0;
-    if (chained) {
+    if constexpr (CHAINED) {
+        const uint64_t obase = ld_relaxed(&hdr->out_base);
         out += obase;
         cap = cap > obase ? cap - obase : 0;
     }
@@ -583,7 +586,7 @@ utf16_to_utf8_kernel(const uint16_t *__restrict__ in, uint64_t n, uint8_t *__res
         res->reserved = 0;
         res->position = pos;
         res->written = written;
-        if (chained) hdr->out_base = obase + written;
+        if constexpr (CHAINED) hdr->out_base = ld_relaxed(&hdr->out_base) + written;
     }
     reset_workspace(hdr, status, status_words);
 }
@@ -744,11 +747,11 @@ uint64_t utf16_to_utf8_tiles(const void *in, uint64_t n)
     return (((uintptr_t)in % 16) / 2 + n + U16Lay::TILE) / U16Lay::TILE;   /* at least one tile */
 }
 
-template <bool VALIDATE, bool BE>
+template <bool VALIDATE, bool BE, bool CHAINED>
 static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64_t cap, void *ws,
-                            uint64_t status_words, DevResult *res, bool chained, int sms, cudaStream_t stream)
+                            uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE, BE>;
+    auto kern = utf16_to_utf8_kernel<U16_THREADS, U16_UPT, U16_STAGES, VALIDATE, BE, CHAINED>;
     static int per_sm = 0;     /* resident CTAs per SM (same for every sm_103 device) */
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U16Lay::SMEM);
@@ -762,7 +765,7 @@ static cudaError_t launch16(const uint16_t *in, uint64_t n, uint8_t *out, uint64
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
     kern<<<(unsigned)grid, U16_THREADS, U16Lay::SMEM, stream>>>(in, n, out, cap, hdr, status,
-                                                                 status_words, tiles, res, chained);
+                                                                 status_words, tiles, res);
     return cudaGetLastError();
 }
 
@@ -770,11 +773,15 @@ cudaError_t launch_utf16_to_utf8(const uint16_t *in, uint64_t n, uint8_t *out, u
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
                                  bool big_endian, bool chained, cudaStream_t stream)
 {
+    if (chained) {   /* the host forms' chunks: validating, little-endian */
+        if (!validate || big_endian) return cudaErrorInvalidValue;
+        return launch16<true, false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
+    }
     if (big_endian)
-        return validate ? launch16<true, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
-                        : launch16<false, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
-    return validate ? launch16<true, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
-                    : launch16<false, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
+        return validate ? launch16<true, true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                        : launch16<false, true, false>(in, n, out, cap, ws, status_words, res, sms, stream);
+    return validate ? launch16<true, false, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch16<false, false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

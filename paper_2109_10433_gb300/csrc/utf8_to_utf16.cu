@@ -178,11 +178,14 @@ struct U8Layout {
  * tile it looks back from, so the CTA holding the smallest unpublished
  * ticket never waits: every wait ends.
  */
-template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE>
-__global__ void __launch_bounds__(THREADS)
+template <int THREADS, int WORDS, int STAGES, bool VALIDATE, bool BE, bool CHAINED>
+/* CHAINED (the host forms' chunks) is a separate instance, held to 5 CTAs
+ * per SM: as a runtime flag, its output base cost the single calls 16
+ * registers and a CTA per SM */
+__global__ void __launch_bounds__(THREADS, CHAINED ? 5 : 0)
 utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__restrict__ out,
                      uint64_t cap, WsHeader *hdr, unsigned long long *status,
-                     uint64_t status_words, uint64_t tiles, DevResult *res, bool chained)
+                     uint64_t status_words, uint64_t tiles, DevResult *res)
 {
     using Lay = U8Layout<THREADS, WORDS, STAGES>;
     constexpr int BPT = Lay::BPT;
@@ -209,8 +212,8 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
     /* a host form's chunks run chained: each writes its output after the
      * units of the chunks before it, which the header holds (the previous
      * chunk's last CTA moved it on) */
-    const uint64_t obase = chained ? ld_relaxed(&hdr->out_base) : 0;
-    if (chained) {
+    if constexpr (CHAINED) {
+        const uint64_t obase = ld_relaxed(&hdr->out_base);
         out += obase;
         cap = cap > obase ? cap - obase : 0;
     }
@@ -640,7 +643,7 @@ utf8_to_utf16_kernel(const uint8_t *__restrict__ in, uint64_t n, uint16_t *__res
         res->reserved = 0;
         res->position = pos;
         res->written = written;
-        if (chained) hdr->out_base = obase + written;
+        if constexpr (CHAINED) hdr->out_base = ld_relaxed(&hdr->out_base) + written;
     }
     reset_workspace(hdr, status, status_words);
 }
@@ -876,11 +879,11 @@ uint64_t utf8_to_utf16_tiles(const void *in, uint64_t n)
     return ((uintptr_t)in % 16 + n + 1 + U8Lay::TILE - 1) / U8Lay::TILE;
 }
 
-template <bool VALIDATE, bool BE>
+template <bool VALIDATE, bool BE, bool CHAINED>
 static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_t cap, void *ws,
-                           uint64_t status_words, DevResult *res, bool chained, int sms, cudaStream_t stream)
+                           uint64_t status_words, DevResult *res, int sms, cudaStream_t stream)
 {
-    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE, BE>;
+    auto kern = utf8_to_utf16_kernel<U8_THREADS, U8_WORDS, U8_STAGES, VALIDATE, BE, CHAINED>;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U8Lay::SMEM);
@@ -894,7 +897,7 @@ static cudaError_t launch8(const uint8_t *in, uint64_t n, uint16_t *out, uint64_
     WsHeader *hdr = static_cast<WsHeader *>(ws);
     auto *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + HEADER_BYTES);
     kern<<<(unsigned)grid, U8_THREADS, U8Lay::SMEM, stream>>>(in, n, out, cap, hdr, status, status_words,
-                                                              tiles, res, chained);
+                                                              tiles, res);
     return cudaGetLastError();
 }
 
@@ -902,11 +905,15 @@ cudaError_t launch_utf8_to_utf16(const uint8_t *in, uint64_t n, uint16_t *out, u
                                  void *ws, uint64_t status_words, DevResult *res, int sms, bool validate,
                                  bool big_endian, bool chained, cudaStream_t stream)
 {
+    if (chained) {   /* the host forms' chunks: validating, little-endian */
+        if (!validate || big_endian) return cudaErrorInvalidValue;
+        return launch8<true, false, true>(in, n, out, cap, ws, status_words, res, sms, stream);
+    }
     if (big_endian)
-        return validate ? launch8<true, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
-                        : launch8<false, true>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
-    return validate ? launch8<true, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream)
-                    : launch8<false, false>(in, n, out, cap, ws, status_words, res, chained, sms, stream);
+        return validate ? launch8<true, true, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                        : launch8<false, true, false>(in, n, out, cap, ws, status_words, res, sms, stream);
+    return validate ? launch8<true, false, false>(in, n, out, cap, ws, status_words, res, sms, stream)
+                    : launch8<false, false, false>(in, n, out, cap, ws, status_words, res, sms, stream);
 }
 
 /* Grid of a streaming pass: the CTAs that fit on the device at once (no

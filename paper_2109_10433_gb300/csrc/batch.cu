@@ -567,7 +567,12 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
     uint64_t carry = 0;
     if (t > 0) carry = block_seg_look_back<THREADS>(d.status, (long long)t, epoch, &hdr->flags, sm);
     if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
-    __threadfence();
+    /* No fence here: the error words a string's result reads were written
+     * by the tiles from the string's first on.  Those tiles' aggregates (or
+     * an inclusive prefix published after their look-back) were read with
+     * acquire loads in the look-back, whose closing barrier hands that
+     * ordering to every thread; this tile's own writes are ordered by the
+     * scan's barriers. */
 
     /* phase B: bytes out, results of strings ending here */
     if (nloc > 0) {
@@ -793,7 +798,12 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
     uint64_t carry = 0;
     if (t > 0) carry = block_seg_look_back<THREADS>(d.status, (long long)t, epoch, &hdr->flags, sm);
     if (tid == 0 && t > 0) st_release(d.status + t, seg_status(epoch, ST_PREFIX, false, tf ? tv : carry + tv));
-    __threadfence();
+    /* No fence here: the error words a string's result reads were written
+     * by the tiles from the string's first on.  Those tiles' aggregates (or
+     * an inclusive prefix published after their look-back) were read with
+     * acquire loads in the look-back, whose closing barrier hands that
+     * ordering to every thread; this tile's own writes are ordered by the
+     * scan's barriers. */
 
     /* phase B, one string piece at a time: units out at each lead (its
      * four bytes from two stage words, those past the string's end

@@ -21,7 +21,7 @@
 #include <cstdint>
 
 #include "common.cuh"
-#include "utf16_scheme.h"
+#include "batch_piece.h"
 #include "kernels.h"
 
 namespace gputf {
@@ -325,18 +325,6 @@ __device__ __forceinline__ int rel_pos(uint64_t x, uint64_t c0, int lim)
     return r < -8 ? -8 : (r > lim ? lim : (int)r);
 }
 
-/* Bit 7 of each byte of m gathered into bits 0-3 (byte k -> bit k). */
-__device__ __forceinline__ uint32_t gather_bit7(uint32_t m)
-{
-    return (((m >> 7) & 0x01010101u) * 0x01020408u) >> 24;
-}
-
-/* Bits [a, b) of a word, 0 <= a < b <= 32. */
-__device__ __forceinline__ uint32_t bit_range(int a, int b)
-{
-    return (b >= 32 ? 0u : (1u << b)) - (1u << a);
-}
-
 /* Stages input elements [x0 - halo, x0 + count - halo) of a direction (bytes
  * `esize` each; zeros outside [0, units)): whole 16-byte vectors when the
  * span lies inside the input and starts 16-byte aligned, else element by
@@ -483,12 +471,9 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
 #define U16AT(x) ((uint32_t)stage[(x) - x0 + HALO])
     /* phase A, one string piece of the chunk at a time (positions j
      * relative to c0): bytes, starts, errors, from bit masks over the
-     * chunk's units.  A piece's bytes are Table 2's closed form (a surrogate
-     * counts 2, so a pair inside the piece gives its 4), corrected where a
-     * pair crosses the chunk's edge: its low half writes nothing here, or
-     * its high half writes all 4.  A unit breaks the pairing rule when it is
-     * high and the next is not low, or low and the one before is not high,
-     * with nothing before a string's first unit or after its last. */
+     * chunk's units (batch_piece.h: Table 2's closed form corrected where a
+     * pair crosses the chunk's edge; the pairing rule with nothing before a
+     * string's first unit or after its last) */
     const int base = tid * UPT + HALO;   /* stage index of c0 */
     const int nloc = (int)(c1 - c0);
     bool f = false;
@@ -506,16 +491,12 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
         uint32_t m80 = 0, m3 = 0, hi = 0, lo = 0;   /* bit k: unit c0 + k */
 #pragma unroll
         for (int g4 = 0; g4 < UPT / 4; g4++) {
-            const uint32_t H = gputf_bperm(w[2 * g4], w[2 * g4 + 1], 0x7531);   /* high bytes */
-            const uint32_t L = gputf_bperm(w[2 * g4], w[2 * g4 + 1], 0x6420);   /* low bytes */
-            const uint32_t ge80 = ~(gputf_zero_bytes(H) & ~L) & 0x80808080u;
-            const uint32_t ge08 = (((H & 0x78787878u) + 0x78787878u) | H) & 0x80808080u;
-            const uint32_t sur = gputf_zero_bytes((H & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
-            const uint32_t t = H << 5;   /* bit 2 of the high byte: a low surrogate */
-            m80 |= gather_bit7(ge80) << (4 * g4);
-            m3 |= gather_bit7(ge08 & ~sur) << (4 * g4);
-            hi |= gather_bit7(sur & ~t) << (4 * g4);
-            lo |= gather_bit7(sur & t) << (4 * g4);
+            uint32_t a, b, h, l;
+            gputf_u16_unit_bits4(w[2 * g4], w[2 * g4 + 1], &a, &b, &h, &l);
+            m80 |= a << (4 * g4);
+            m3 |= b << (4 * g4);
+            hi |= h << (4 * g4);
+            lo |= l << (4 * g4);
         }
         const bool pu_hi = is_hi16(stage[base - 1]), nu_lo = is_lo16(stage[base + nloc]);
         uint64_t ss = s, st = off_at(d, sm, ss), en = off_at(d, sm, ss + 1);
@@ -531,21 +512,16 @@ __device__ void batch16_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHe
                 enl = rel_pos(en, c0, UPT + 8);
             }
             const int pe = enl < nloc ? enl : nloc;   /* the piece [j, pe) */
-            const uint32_t pm = bit_range(j, pe), fb = 1u << j, lb = 1u << (pe - 1);
             if (j == stl) {
                 f = true;
                 v = 0;
             }
             /* a piece starts at its string's start or at the chunk's start,
              * and ends at its string's end or at the chunk's end */
-            const bool ph = j != stl && pu_hi;                    /* the unit before the piece is high */
-            const bool nl = pe != enl && nu_lo;                   /* the unit after the piece is low */
-            v += __popc(pm) + __popc(m80 & pm) + __popc(m3 & pm);
-            if ((lo & fb) && ph) v -= 2;
-            if ((hi & lb) && nl) v += 2;
-            const uint32_t prevhi = ((hi << 1) & ~fb) | (ph ? fb : 0u);
-            const uint32_t nextlo = ((lo >> 1) & ~lb) | (nl ? lb : 0u);
-            const uint32_t bad = ((hi & ~nextlo) | (lo & ~prevhi)) & pm;
+            const bool ph = j != stl && pu_hi;   /* the unit before the piece is high */
+            const bool nl = pe != enl && nu_lo;   /* the unit after the piece is low */
+            uint32_t bad;
+            v += gputf_u16_piece(m80, m3, hi, lo, j, pe, ph, nl, &bad);
             if (bad && err_s != ss) {
                 record_string_error(d.errw, ss, epoch, c0 + (__ffs(bad) - 1) - st);
                 err_s = ss;
@@ -733,10 +709,10 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
             const uint32_t x = sw[k];
             const uint32_t nz = gputf_nonzero_bytes(gputf_utf8_errors_step(&u8s, x));
             fl |= ((((nz >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
-            const uint32_t ld = ~(x & ~(x << 1)) & 0x80808080u;
-            const uint32_t f4 = x & (x << 1) & (x << 2) & (x << 3) & 0x80808080u;
-            lb |= ((((ld >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
-            fb |= ((((f4 >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+            uint32_t l4, f4;
+            gputf_u8_lead_bits(x, &l4, &f4);
+            lb |= l4 << (4 * k);
+            fb |= f4 << (4 * k);
         }
     }
     /* phase A, one string piece of the chunk at a time (positions j
@@ -759,12 +735,12 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
                 enl = rel_pos(en, c0, BPT + 8);
             }
             const int pe = enl < nloc ? enl : nloc;   /* the piece [j, pe) */
-            const uint32_t pm = bit_range(j, pe);
+            const uint32_t pm = gputf_bit_range(j, pe);
             if (j == stl) {
                 f = true;
                 v = 0;
             }
-            v += __popc(lb & pm) + __popc(fb & pm);
+            v += gputf_u8_piece_units(lb, fb, j, pe);
             /* the string's first three bytes see only its own bytes before
              * them (zeros before its start): their flags are taken exactly */
             uint32_t fm = fl & pm;
@@ -827,7 +803,7 @@ __device__ void batch8_tile(const BatchDir &d, uint64_t t, unsigned epoch, WsHea
             if (j == stl) g = 0;
             const int pe = enl < nloc ? enl : nloc;
             if (wr) {
-                uint32_t lm = lb & bit_range(j, pe);
+                uint32_t lm = lb & gputf_bit_range(j, pe);
                 while (lm) {
                     const int k = __ffs(lm) - 1;
                     lm &= lm - 1;

@@ -14,7 +14,7 @@
 #include <string.h>
 
 #include "oracle.c"
-#include "utf16_scheme.h"   /* includes utf8_scheme.h */
+#include "batch_piece.h"    /* includes utf16_scheme.h and utf8_scheme.h */
 
 static uint64_t rng_state = 0x9E3779B97F4A7C15ull;
 
@@ -148,6 +148,36 @@ int main(void)
         }
         drive_utf8(b, n);
         drive_utf16(u, n);
+    }
+    /* the batched kernel's per-piece arithmetic: every piece of random
+     * 32-unit (and 32-byte) chunks, with both neighbour cases */
+    for (int t = 0; t < 200; t++) {
+        uint32_t m80 = 0, m3 = 0, hi = 0, lo = 0, lb = 0, fb = 0;
+        for (int g = 0; g < 8; g++) {
+            uint32_t w[2];
+            for (int i = 0; i < 2; i++) {
+                const uint64_t r = next_rand();
+                const uint32_t u0 = r % 3 == 0 ? (0xD800u | ((r >> 8) & 0x7FF)) : (uint32_t)((r >> 20) & 0xFFFF);
+                const uint32_t u1 = (r >> 40) % 3 == 0 ? (0xD800u | ((r >> 44) & 0x7FF)) : (uint32_t)((r >> 48) & 0xFFFF);
+                w[i] = u0 | (u1 << 16);
+            }
+            uint32_t a, b4, h, l, l4, f4;
+            gputf_u16_unit_bits4(w[0], w[1], &a, &b4, &h, &l);
+            m80 |= a << (4 * g);
+            m3 |= b4 << (4 * g);
+            hi |= h << (4 * g);
+            lo |= l << (4 * g);
+            gputf_u8_lead_bits((uint32_t)next_rand(), &l4, &f4);
+            lb |= l4 << (4 * g);
+            fb |= f4 << (4 * g);
+        }
+        for (int j = 0; j < 32; j++)
+            for (int pe = j + 1; pe <= 32; pe++) {
+                uint32_t bad;
+                (void)gputf_u16_piece(m80, m3, hi, lo, j, pe, (pe + t) & 1, (j + t) & 1, &bad);
+                (void)gputf_u8_piece_units(lb, fb, j, pe);
+            }
+        calls += 2;
     }
     /* the loops over many strings */
     {

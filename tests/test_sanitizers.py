@@ -3,7 +3,8 @@ and UndefinedBehaviorSanitizer.
 
 tests/native/sanitize_driver.c calls the oracle's transcoders, validators and
 length functions, and the headers' UTF-8 check, fix-up, decoder and UTF-16
-classification and byte arithmetic, on every string of up to two bytes,
+classification and byte arithmetic, and the batched kernel's per-piece
+arithmetic over every piece of random chunks, on every string of up to two bytes,
 every scalar value, and 20,000 random inputs rich in continuation bytes,
 leads and surrogates, each in a buffer of exactly the size the call is given
 and with every capacity from none to ample.  Built with
